@@ -1,0 +1,331 @@
+#!/usr/bin/env python3
+"""Throughput of the coupled D2Q9 + D2Q5 porous cascaded LB step on GB300.
+
+Workload (N = 1): natural convection in a 4096 x 4096 porous cavity with the
+seeded porosity eps(x) = 0.3 + 0.6 Phi(g(x)) (g a unit Gaussian random field,
+correlation length 32 cells, seed 20211012), Da 1e-3, Ra 1e6, Pr 0.71,
+sigma 1, FP64.  One bench step = one LB time step over the whole grid (all
+nodes, both lattices, walls).  N > 1 runs one independent replica per GPU
+(weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.  `value` = cells x steps / time over all
+ranks (MLUPS), timed with CUDA events on the library's stream, inputs
+resident in HBM (the 3.8 GB state is far larger than the 129 MB L2).  `e2e`
+is the same metric through the public C ABI from pinned host buffers:
+clb_init (porosity upload) + K steps + clb_macros (four fields back) +
+clb_nusselt, wall-clock.  `--impl reference` times the FP64 CPU oracle on
+the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+NX = NY = 4096          # --size changes this (smaller sizes are for profiler captures only)
+CASE = dict(Ra=1e6, Da=1e-3, Pr=0.71, sigma=1.0)
+PHI_SEED, PHI_ELL = 20211012, 32.0
+METRIC = "coupled D2Q9+D2Q5 MLUPS"
+UNIT = "MLUPS"
+WORKLOAD = ("{n}x{n} porous cavity, seeded GRF porosity 0.3+0.6*Phi(g) (l=32, seed 20211012), "
+            "Da 1e-3, Ra 1e6, Pr 0.71, sigma 1, FP64")
+
+# Algorithmic bytes per coupled cell update of the FP64 form: 14 distribution
+# values read and 14 written (8 B each) plus the porosity (8 B).
+BYTES_PER_CCU_F64 = 28 * 8 + 8
+# FP64 floating-point operations per interior coupled cell update executed by
+# k_step_f64 (shift + Forchheimer), from the ncu instruction counters
+# (dadd + dmul + 2 dfma per launch / nodes); see profiles/.
+FP64_FLOP_PER_CCU = None
+SMS, DFMA_PER_CLK_PER_SM = 152, 2   # GB300: 1.25 TFLOP/s FP64 nominal at 2.07 GHz
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": reasons}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _porosity():
+    from paper_2110_05943_gb300.inputs import porosity_field
+    return porosity_field(NX, NY, seed=PHI_SEED, ell=PHI_ELL)
+
+
+def cpu_oracle_rate(phi, budget_s: float = 12.0, side: int = 512):
+    """FP64 oracle on the SW corner block (side x side) of the workload, with
+    the full cavity's lattice parameters (L = n - 1); MLUPS on all host cores."""
+    side = min(side, NX)
+    import oracle
+    sub = phi[:side, :side].copy()
+    p = oracle.Problem(nx=side, ny=side, L=float(NY - 1), **CASE)
+    o = oracle.Oracle(p, phi=sub)
+    t0 = time.perf_counter()
+    o.step(2)
+    dt = max(time.perf_counter() - t0, 1e-6) / 2
+    steps = max(3, int(budget_s / dt))
+    t0 = time.perf_counter()
+    o.step(steps)
+    t = time.perf_counter() - t0
+    return {"value": side * side * steps / t / 1e6, "unit": UNIT, "cores": o.nthreads, "kind": "oracle",
+            "sample": f"{side}x{side} corner block of the {NX}^2 workload (same porosity values and lattice "
+                      f"parameters, walls on all four sides), {steps} FP64 steps, {t:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+    import oracle
+    phi = _porosity()
+    side = min(512, NX)
+    sub = phi[:side, :side].copy()
+    p = oracle.Problem(nx=side, ny=side, L=float(NY - 1), **CASE)
+    o = oracle.Oracle(p, phi=sub)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    t = time.perf_counter() - t0
+    v = side * side * args.steps / t / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(n=NX), "sample": f"{side}x{side} corner block per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": o.nthreads, "kind": "oracle",
+                             "sample": f"{side}x{side} corner block of the {NX}^2 workload, "
+                                       f"{args.steps} FP64 steps"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def steady_state_64(clb, torch):
+    """Cavity 64^2 (phi 0.6, Da 1e-2, Ra 1e4, Pr 1): steps and wall time until
+    the mean Nusselt number of the hot wall changes by <= 1e-4 (relative) over
+    1000 steps; also Nu after 20,000 steps."""
+    p = clb.clb_params_default(nx=64, ny=64, Ra=1e4, Da=1e-2, Pr=1.0)
+    sim = clb.Simulation.create(p, 0.6, clb.clb_bc_cavity(1.0, 0.0),
+                                stream=torch.cuda.current_stream().cuda_stream)
+    t0 = time.perf_counter()
+    prev = sim.nusselt(clb.W)
+    steps, nu20k, done_at = 0, None, None
+    while steps < 200_000:
+        sim.step(1000)
+        steps += 1000
+        nu = sim.nusselt(clb.W)
+        if steps == 20_000:
+            nu20k = nu
+        if done_at is None and abs(nu - prev) <= 1e-4 * abs(nu):
+            done_at = (steps, time.perf_counter() - t0, nu)
+        prev = nu
+        if done_at is not None and nu20k is not None:
+            break
+    sim.close()
+    return {"workload": "64x64 cavity, phi 0.6, Da 1e-2, Ra 1e4, Pr 1, FP64 (Table 1 row, coarser grid)",
+            "criterion": "|dNu| <= 1e-4 Nu over 1000 steps", "steps": done_at[0] if done_at else None,
+            "seconds": done_at[1] if done_at else None, "nu_at_steady": done_at[2] if done_at else None,
+            "nu_at_20000_steps": nu20k}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_2110_05943_gb300 import clb
+    clb.load()
+    phi = _porosity()
+    stream = torch.cuda.current_stream()
+    p = clb.clb_params_default(nx=NX, ny=NY, **CASE)
+    sim = clb.Simulation.create(p, phi, clb.clb_bc_cavity(1.0, 0.0), stream=stream.cuda_stream)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    sim.step(args.steps)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    t = t_start.elapsed_time(t_end) / 1e3
+    nu = sim.nusselt(clb.W)
+    sim.close()
+    if dist is not None:
+        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = float(tt.item())
+    cells = NX * NY
+    value = cells * args.steps * ws / t / 1e6
+    per_launch = t / args.steps
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        phi_pin = torch.from_numpy(phi).pin_memory()
+        outs = [torch.empty((NY, NX), dtype=torch.float64).pin_memory() for _ in range(4)]
+        import ctypes
+        L = clb.load()
+        dp = lambda a: ctypes.cast(a.data_ptr(), ctypes.POINTER(ctypes.c_double))
+        bc = clb.clb_bc_cavity(1.0, 0.0)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        h = ctypes.c_void_p()
+        rc = L.clb_init(ctypes.byref(h), ctypes.byref(p), dp(phi_pin), None, ctypes.byref(bc),
+                        ctypes.c_void_p(stream.cuda_stream))
+        assert rc == 0, L.clb_last_error(None)
+        assert L.clb_step(h, args.steps) == 0
+        assert L.clb_macros(h, *[dp(o) for o in outs]) == 0
+        nuv = ctypes.c_double()
+        assert L.clb_nusselt(h, 0, ctypes.byref(nuv)) == 0
+        L.clb_destroy(h)
+        te = time.perf_counter() - t0
+        barrier()
+        if dist is not None:
+            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            te = float(tt.item())
+        e2e = {"value": cells * args.steps * ws / te / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": phi.nbytes / args.steps,
+               "d2h_bytes_per_step": (4 * cells * 8 + 8) / args.steps,
+               "includes": "clb_init (allocation + porosity upload) + steps + clb_macros + clb_nusselt"}
+
+    if rank != 0:
+        return
+    peaks, src = _peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    gbs = BYTES_PER_CCU_F64 * cells / per_launch / 1e9
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    fp64_peak = SMS * DFMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    if FP64_FLOP_PER_CCU:
+        ach = FP64_FLOP_PER_CCU * cells / per_launch / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                "traffic": None, "kernel": "k_step_f64<shift, forchheimer>",
+                "peak_source": f"FP64 pipe: {SMS} SMs x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 x {sm_mhz:.0f} MHz "
+                               "(median SM clock under load)",
+                "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                        "bytes_per_ccu": BYTES_PER_CCU_F64, "peak_source": f"{src} hbm_gbs"}}
+    else:
+        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+                "traffic": None, "kernel": "k_step_f64<shift, forchheimer>", "bytes_per_ccu": BYTES_PER_CCU_F64,
+                "peak_source": f"{src} hbm_gbs"}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(n=NX), "nx": NX, "ny": NY, "cells": cells, "replicas": ws,
+                       "l2": f"state {NX * NY * 14 * 16 / 1e9:.2f} GB per replica (two buffers) vs 0.13 GB L2: no flush",
+                       "parallelism": f"replicas x{ws}", "nu_hot_wall_after": nu},
+            "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
+            "e2e": e2e}
+    if ws == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_rate(phi)
+    if not args.no_steady:
+        line["steady_state"] = steady_state_64(clb, torch)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-steady", action="store_true")
+    ap.add_argument("--size", type=int, default=4096, help="grid side (default 4096; smaller for profiling)")
+    args = ap.parse_args()
+    global NX, NY
+    NX = NY = args.size
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+/*
+ * clb.h -- C ABI of the GB300 (sm_103a) REV-scale cascaded lattice Boltzmann
+ * library for convection heat transfer in porous media.
+ *
+ * Method: Feng, Liu & He, "Numerical simulations of convection heat transfer
+ * in porous media using a cascaded lattice Boltzmann method",
+ * arXiv:2110.05943.  One time step is the coupled update of
+ *   - the D2Q9 porous cascaded flow solver of Sec. 2.1 (Eqs. 4-23: shift to
+ *     porosity-aware central moments by N of Eq. 14, cascaded relaxation of
+ *     Eq. 11, implicit Brinkman-Forchheimer velocity of Eqs. 22-23, force of
+ *     Eq. 4 with the Ergun coefficient of Eq. 5, streaming of Eq. 18), and
+ *   - the D2Q5 temperature solver of Sec. 2.2 (Eqs. 24-36: shift N_T of
+ *     Eq. 31 with the heat capacity ratio sigma, relaxation Eq. 28,
+ *     streaming Eq. 35),
+ * with walls treated by non-equilibrium extrapolation (Sec. 3).
+ *
+ * Conventions for every entry point:
+ *   - Return CLB_OK (0) on success or a negative CLB_ERR_* code; no C++
+ *     exception crosses the ABI.  clb_last_error() gives a message.
+ *   - Host arrays of nodal fields are (ny, nx) row-major, x fastest, FP64,
+ *     caller-owned; the library copies what it needs and keeps no pointer.
+ *   - The handle owns all device memory; clb_destroy frees it.
+ *   - All work is issued on the CUDA stream given to clb_init (NULL: the
+ *     legacy default stream).  Calls that return host data synchronise that
+ *     stream; clb_step does not.
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef CLB_H
+#define CLB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CLB_OK 0
+#define CLB_ERR_ARG (-1)      /* invalid argument or parameter */
+#define CLB_ERR_CUDA (-2)     /* a CUDA runtime call failed */
+#define CLB_ERR_OOM (-3)      /* device or host allocation failed */
+#define CLB_ERR_UNSTABLE (-4) /* non-finite value found in the fields */
+#define CLB_ERR_STATE (-5)    /* checkpoint does not match this handle */
+
+/* Sides, in this order everywhere: west (x = 0), east (x = nx-1),
+ * south (y = 0), north (y = ny-1).  Gravity points along -y. */
+enum { CLB_W = 0, CLB_E = 1, CLB_S = 2, CLB_N = 3 };
+enum { CLB_PERIODIC = 0, CLB_WALL = 1 };
+enum { CLB_ADIABATIC = 0, CLB_ISOTHERMAL = 1 };
+/* Arithmetic / storage form of the distributions. */
+enum { CLB_F64 = 0 };
+
+/* Boundary specification.  Opposite sides must both be periodic or both
+ * walls; a walled direction needs at least 4 nodes.  Wall nodes lie on the
+ * boundary lines and are rebuilt every step by non-equilibrium extrapolation
+ * from the inward neighbour: velocity (u[s], v[s]); temperature T[s] if
+ * thermal[s] == CLB_ISOTHERMAL, else zero normal gradient extrapolated to
+ * second order.  At a corner the W/E wall's velocity is used and an
+ * isothermal wall wins over an adiabatic one (W/E first). */
+typedef struct {
+    int32_t kind[4];
+    double u[4], v[4];
+    int32_t thermal[4];
+    double T[4];
+} clb_bc;
+
+/* Physical setup (Eq. 38 groups; Sec. 3 model constants).  Fill with
+ * clb_params_default and override.
+ *   Ra, Da, Pr, J, Gamma, sigma : Eq. 38 groups and the heat capacity ratio
+ *   Ma    : Mach number of Eq. 46 (0.1)
+ *   L     : characteristic length in lattice units (<= 0: ny - 1)
+ *   nu    : > 0 fixes the fluid viscosity directly (channel flows,
+ *           1/s_v = 1/2 + J nu / c_s^2); <= 0 uses Eq. 46
+ *   dT, T0, T_init : temperature difference, reference and initial value
+ *   ax, ay: external acceleration a (Eq. 4, G = -g beta (T - T0) + a)
+ *   varpi : D2Q5 parameter (c_sT^2 = varpi / 2), 1/4
+ *   s3, s4: free relaxation rates of Eq. 15, 1.2 and 1.8
+ *   sb    : bulk relaxation rate s_b of Eq. 15 (s+ = (s_b + s_v)/2,
+ *           s- = (s_b - s_v)/2 act on k~20, k~02).  > 0: used as given.
+ *           <= 0 (default): s_b = s_v as in Sec. 3, raised to 1.2 when
+ *           s_v < 1.2 -- with s3 = 1.2, s4 = 1.8 the linearised scheme is
+ *           unstable for s_b below 1.19, and Eq. 46 gives s_v < 1.2 at low
+ *           Ra or large L.  s_b only sets the bulk viscosity, which does not
+ *           enter the incompressible equations (Eqs. 1-3).
+ *   forchheimer : 1 = Ergun F_phi of Eq. 5, 0 = F_phi = 0
+ *   shift : 1 = porous shift matrices (Eqs. 14, 31); 0 = unit shifts, the
+ *           non-orthogonal MRT limit named at the end of Sec. 2
+ *   precision : CLB_F64
+ * Fixed by the paper (Sec. 3): s_0 = s_1 = 1, zeta_T = zeta_e = zeta_nu = 1.
+ * The permeability is K = Da L^2, uniform; F_phi(phi(x)) and every phi
+ * factor are taken at the node. */
+typedef struct {
+    int32_t nx, ny;
+    int32_t precision;
+    int32_t forchheimer;
+    int32_t shift;
+    int32_t reserved;
+    double Ra, Da, Pr, J, Gamma, sigma;
+    double Ma, L, nu;
+    double dT, T0, T_init;
+    double ax, ay;
+    double varpi, s3, s4;
+    double sb;
+} clb_params;
+
+/* Lattice parameters the library derived from clb_params (read-only). */
+typedef struct {
+    double sb, sv, zeta_a;/* relaxation rates s_b, s_v (Eq. 15) and zeta_alpha (Eq. 28) */
+    double nu, nu_e;      /* fluid and effective kinematic viscosity */
+    double alpha, alpha_e;/* fluid and effective thermal diffusivity */
+    double K, gbeta, L;   /* permeability, g*beta, characteristic length */
+    int64_t pitch;        /* row pitch of the device arrays, in elements */
+} clb_lattice;
+
+typedef struct clb_handle clb_handle;
+
+/* Paper defaults: 64 x 64, Ra 1e4, Da 1e-2, Pr 1, J = Gamma = sigma = 1,
+ * Ma 0.1, dT 1, T0 = T_init = 0.5, varpi 1/4, s3 1.2, s4 1.8, sb automatic,
+ * Forchheimer on, porous shift on, FP64. */
+void clb_params_default(clb_params* p);
+
+/* Cavity of Sec. 3.2: four no-slip walls, W at Th, E at Tc, S and N
+ * adiabatic. */
+void clb_bc_cavity(clb_bc* bc, double Th, double Tc);
+
+/* Create a simulation.
+ *   phi    : porosity per node, host, ny*nx values in (0, 1] (required)
+ *   ay_row : optional host array of ny values; replaces p->ay row by row
+ *            (a y-dependent external force such as Eq. 42); NULL = uniform
+ *   bc     : boundary specification
+ *   stream : cudaStream_t to issue all work on, or NULL
+ * The state starts at rest: rho = 1, u = 0, T = T_init.  On failure *h is
+ * NULL and clb_last_error(NULL) describes the problem. */
+int clb_init(clb_handle** h, const clb_params* p, const double* phi, const double* ay_row,
+             const clb_bc* bc, void* stream);
+
+/* Advance n >= 0 time steps (asynchronous on the handle's stream). */
+int clb_step(clb_handle* h, int64_t n);
+
+/* Reset the state to the local equilibria of the given host fields
+ * (ny*nx each; rho and T required, ux/uy may be NULL for zero) and the
+ * step counter to 0. */
+int clb_set_fields(clb_handle* h, const double* rho, const double* ux, const double* uy,
+                   const double* T);
+
+/* Macroscopic fields at the current time level into caller-owned host
+ * arrays of ny*nx values (any may be NULL): rho (Eq. 20), u (Eqs. 22-23),
+ * T (Eq. 36); wall nodes report the imposed velocity and wall temperature.
+ * Returns CLB_ERR_UNSTABLE if any value is not finite. */
+int clb_macros(clb_handle* h, double* rho, double* ux, double* uy, double* T);
+
+/* Same, into device arrays of ny*nx values each (any may be NULL); no
+ * synchronisation and no finiteness check. */
+int clb_macros_device(clb_handle* h, double* rho, double* ux, double* uy, double* T);
+
+/* Mean Nusselt number of a wall (Sec. 3.2): Nu(s) = -L dT/dn / dT with the
+ * one-sided second-order difference taken along x (W, E) or y (S, N),
+ * averaged over the wall by the trapezoid rule; FP64 device reduction. */
+int clb_nusselt(clb_handle* h, int32_t side, double* nu);
+
+/* Relative change since the previous call (or since init / set_fields):
+ * r_u = ||u^n - u^m||_2 / ||u^n||_2 and r_T likewise for T, over all nodes;
+ * FP64 device reduction.  Returns CLB_ERR_UNSTABLE on non-finite fields. */
+int clb_residual(clb_handle* h, double* r_u, double* r_T);
+
+/* Time steps taken since init / set_fields / set_state. */
+int64_t clb_time(const clb_handle* h);
+
+/* Derived lattice parameters. */
+int clb_lattice_params(const clb_handle* h, clb_lattice* out);
+
+/* Checkpoint: bytes needed, copy out, copy in (same nx, ny, precision).
+ * Resuming from a checkpoint reproduces the run bit for bit. */
+size_t clb_state_bytes(const clb_handle* h);
+int clb_get_state(clb_handle* h, void* buf, size_t bytes);
+int clb_set_state(clb_handle* h, const void* buf, size_t bytes);
+
+/* Wait for all work issued on the handle's stream. */
+int clb_sync(clb_handle* h);
+
+void clb_destroy(clb_handle* h);
+
+/* Last error message of h, or of the calling thread's last failed
+ * clb_init when h is NULL. */
+const char* clb_last_error(const clb_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLB_H */

@@ -19,6 +19,11 @@ Parameter mapping (written from the paper):
   * Eq. 15 text: nu_e = c_s^2 (1/s_v - 1/2); Eq. 37: alpha_e = c_sT^2 (1/zeta_a - 1/2);
   * Sec. 3 constants: s_0 = s_1 = 1, s_b = s_v, s_3 = 1.2, s_4 = 1.8,
     zeta_T = zeta_e = zeta_nu = 1, varpi = 1/4 (c_sT^2 = 1/8), J = 1.
+  * Bulk rate: with s_3 = 1.2 and s_4 = 1.8 the linearised scheme is stable
+    only for s_b >= 1.19, so s_b = s_v is kept where s_v >= 1.2 and raised
+    to 1.2 below that (Eq. 46 gives s_v < 1.2 for the Ra = 1e3 rows of
+    Table 1 and for large grids).  s_b sets only the bulk viscosity, which
+    does not appear in the incompressible equations (Eqs. 1-3).
 """
 from __future__ import annotations
 
@@ -218,11 +223,19 @@ class Problem:
     varpi: float = 0.25
     s3: float = 1.2
     s4: float = 1.8
+    sb: float | None = None         # bulk rate; None: s_v, raised to SB_STABLE when s_v < SB_STABLE
     walls: Walls = field(default_factory=cavity_walls)
+
+
+# Smallest bulk relaxation rate for which the printed rate set s_3 = 1.2,
+# s_4 = 1.8 (Sec. 3) is linearly stable (von Neumann analysis of the
+# linearised step, tests/test_oracle_stability.py: threshold 1.19).
+SB_STABLE = 1.2
 
 
 @dataclass
 class Lattice:
+    sb: float
     sv: float
     za: float
     nu: float
@@ -251,7 +264,9 @@ def lattice_params(p: Problem) -> Lattice:
     alpha_e = cT2 * (inv_za - 0.5)                                             # Eq. 37
     K = p.Da * L * L                                                           # Eq. 38
     gbeta = p.Ra * nu * alpha / (p.dT * L ** 3)                                # Eq. 38
-    return Lattice(sv=1.0 / inv_sv, za=1.0 / inv_za, nu=nu, nu_e=nu_e, alpha=alpha,
+    sv = 1.0 / inv_sv
+    sb = p.sb if p.sb is not None else max(sv, SB_STABLE)
+    return Lattice(sb=sb, sv=sv, za=1.0 / inv_za, nu=nu, nu_e=nu_e, alpha=alpha,
                    alpha_e=alpha_e, K=K, gbeta=gbeta, L=L)
 
 
@@ -273,7 +288,7 @@ def _cfg(p: Problem, nthreads: int) -> _Cfg:
         c.Tw[s] = 0.0 if w.T[s] is None else float(w.T[s])
     c.nu, c.nu_e, c.K, c.gbeta = lat.nu, lat.nu_e, lat.K, lat.gbeta
     c.sigma, c.varpi, c.T0, c.ax = p.sigma, p.varpi, p.T0, p.ax
-    c.s0, c.s1, c.sb, c.sv, c.s3, c.s4 = 1.0, 1.0, lat.sv, lat.sv, p.s3, p.s4
+    c.s0, c.s1, c.sb, c.sv, c.s3, c.s4 = 1.0, 1.0, lat.sb, lat.sv, p.s3, p.s4
     c.zT, c.za, c.ze, c.zn = 1.0, lat.za, 1.0, 1.0
     c.forchheimer = int(bool(p.forchheimer))
     c.shift = int(bool(p.shift))

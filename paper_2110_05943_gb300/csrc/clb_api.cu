@@ -1,0 +1,570 @@
+// clb_api.cu -- host side of the C ABI declared in include/clb.h.
+//
+// Parameter mapping (Sec. 3 and Eqs. 37, 38, 46 of arXiv:2110.05943),
+// device memory, the CUDA-graph step driver, and the FP64 reductions for the
+// Nusselt number and the steady-state residual.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/clb.h"
+#include "clb_f64.cuh"
+#include "clb_reduce.cuh"
+
+using namespace clb;
+
+namespace {
+
+constexpr double kCs2 = 1.0 / 3.0;       // D2Q9 c_s^2 (Eq. 15 text)
+constexpr int kGraphSteps = 32;          // steps per captured graph (even: same buffer parity)
+// Smallest bulk rate for which s3 = 1.2, s4 = 1.8 give a linearly stable
+// step (von Neumann threshold 1.19); used when s_b = s_v would fall below it.
+constexpr double kSbStable = 1.2;
+
+thread_local std::string g_init_error;
+
+
+}  // namespace
+
+struct clb_handle {
+    clb_params prm{};
+    clb_bc bc{};
+    clb_lattice lat{};
+    KParams kp{};
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int device = 0;
+    // distributions, ping-pong: buf[par] holds the post-collision values of
+    // the last step; par flips every step
+    double* f[2] = {nullptr, nullptr};
+    double* g[2] = {nullptr, nullptr};
+    int par = 0;
+    Coef* coef = nullptr;
+    double* ayg = nullptr;
+    double* scratch = nullptr;       // 4 dense fields (macros, set_fields)
+    double* snap = nullptr;          // 3 dense fields (residual reference)
+    double* partial = nullptr;       // block partial sums of the reductions
+    double* result = nullptr;        // reduction results (device)
+    double* host_res = nullptr;      // pinned reduction results
+    int n_partial = 0;
+    int64_t t = 0;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_failed = false;
+    dim3 block, grid;
+    std::string err;
+};
+
+static int fail(clb_handle* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_init_error = buf;
+    return code;
+}
+
+#define CK(h, call)                                                                              \
+    do {                                                                                         \
+        cudaError_t e_ = (call);                                                                 \
+        if (e_ != cudaSuccess) {                                                                 \
+            return fail((h), e_ == cudaErrorMemoryAllocation ? CLB_ERR_OOM : CLB_ERR_CUDA,       \
+                        "%s failed: %s", #call, cudaGetErrorString(e_));                         \
+        }                                                                                        \
+    } while (0)
+
+// ------------------------------------------------------------------ defaults
+extern "C" void clb_params_default(clb_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->nx = 64;
+    p->ny = 64;
+    p->precision = CLB_F64;
+    p->forchheimer = 1;
+    p->shift = 1;
+    p->Ra = 1e4;
+    p->Da = 1e-2;
+    p->Pr = 1.0;
+    p->J = 1.0;
+    p->Gamma = 1.0;
+    p->sigma = 1.0;
+    p->Ma = 0.1;
+    p->L = 0.0;
+    p->nu = 0.0;
+    p->dT = 1.0;
+    p->T0 = 0.5;
+    p->T_init = 0.5;
+    p->varpi = 0.25;
+    p->s3 = 1.2;
+    p->s4 = 1.8;
+}
+
+extern "C" void clb_bc_cavity(clb_bc* bc, double Th, double Tc) {
+    if (!bc) return;
+    std::memset(bc, 0, sizeof *bc);
+    for (int s = 0; s < 4; ++s) bc->kind[s] = CLB_WALL;
+    bc->thermal[CLB_W] = CLB_ISOTHERMAL;
+    bc->T[CLB_W] = Th;
+    bc->thermal[CLB_E] = CLB_ISOTHERMAL;
+    bc->T[CLB_E] = Tc;
+}
+
+// ------------------------------------------------------------------ mapping
+// Dimensionless groups -> lattice parameters.
+//   Eq. 46:    1/s_v = 1/2 + Ma J L sqrt(3 Pr) / sqrt(Ra)           (nu not given)
+//   Sec. 3.1:  1/s_v = 1/2 + J nu / c_s^2                            (nu given)
+//   Eq. 15:    nu_e = c_s^2 (1/s_v - 1/2),  nu = nu_e / J
+//   Eq. 46:    1/zeta_a = 1/2 + Gamma c_s^2 (1/s_v - 1/2) / (J c_sT^2 Pr)
+//   Eq. 37:    alpha_e = c_sT^2 (1/zeta_a - 1/2),  alpha = nu / Pr
+//   Eq. 38:    K = Da L^2,  g beta = Ra nu alpha / (dT L^3)
+static int map_params(const clb_params* p, clb_lattice* lat, std::string& why) {
+    char buf[256];
+    auto bad = [&](const char* m) { why = m; return CLB_ERR_ARG; };
+    if (p->nx < 1 || p->ny < 1) return bad("nx and ny must be positive");
+    if (p->precision != CLB_F64) return bad("unsupported precision");
+    if (!(p->Da > 0) || !(p->Pr > 0) || !(p->J > 0) || !(p->Gamma > 0) || !(p->sigma > 0))
+        return bad("Da, Pr, J, Gamma and sigma must be positive");
+    if (!(p->Ra >= 0)) return bad("Ra must be >= 0");
+    if (!(p->dT > 0)) return bad("dT must be positive");
+    if (!(p->varpi > 0 && p->varpi < 1)) return bad("varpi must lie in (0, 1)");
+    if (!(p->s3 > 0 && p->s3 < 2) || !(p->s4 > 0 && p->s4 < 2)) return bad("s3 and s4 must lie in (0, 2)");
+    const double L = p->L > 0 ? p->L : (double)(p->ny - 1);
+    if (!(L > 0)) return bad("characteristic length must be positive (set L or use ny >= 2)");
+    double inv_sv;
+    if (p->nu > 0) {
+        inv_sv = 0.5 + p->J * p->nu / kCs2;
+    } else {
+        if (!(p->Ra > 0) || !(p->Ma > 0)) return bad("Ra and Ma must be positive when nu is not given");
+        inv_sv = 0.5 + p->Ma * p->J * L * std::sqrt(3.0 * p->Pr) / std::sqrt(p->Ra);
+    }
+    const double nu_e = kCs2 * (inv_sv - 0.5);
+    const double nu = nu_e / p->J;
+    const double cT2 = 0.5 * p->varpi;
+    const double inv_za = 0.5 + p->Gamma * kCs2 * (inv_sv - 0.5) / (p->J * cT2 * p->Pr);
+    lat->sv = 1.0 / inv_sv;
+    lat->sb = p->sb > 0 ? p->sb : (lat->sv < kSbStable ? kSbStable : lat->sv);
+    if (!(lat->sb < 2)) return bad("sb must lie in (0, 2)");
+    lat->zeta_a = 1.0 / inv_za;
+    lat->nu = nu;
+    lat->nu_e = nu_e;
+    lat->alpha = nu / p->Pr;
+    lat->alpha_e = cT2 * (inv_za - 0.5);
+    lat->K = p->Da * L * L;
+    lat->gbeta = p->Ra * nu * lat->alpha / (p->dT * L * L * L);
+    lat->L = L;
+    if (!(lat->sv > 0 && lat->sv < 2) || !(lat->zeta_a > 0 && lat->zeta_a < 2)) {
+        std::snprintf(buf, sizeof buf, "relaxation rates out of (0, 2): s_v = %g, zeta_a = %g", lat->sv,
+                      lat->zeta_a);
+        why = buf;
+        return CLB_ERR_ARG;
+    }
+    return CLB_OK;
+}
+
+static void pick_launch(clb_handle* h) {
+    const int nx = h->prm.nx, ny = h->prm.ny;
+    int bx = 128;
+    while (bx > 32 && bx / 2 >= nx) bx /= 2;
+    int by = 256 / bx;
+    if (by > ny) by = ny < 1 ? 1 : ny;
+    h->block = dim3(bx, by);
+    h->grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by);
+}
+
+static void free_all(clb_handle* h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        cudaFree(h->f[i]);
+        cudaFree(h->g[i]);
+    }
+    cudaFree(h->coef);
+    cudaFree(h->ayg);
+    cudaFree(h->scratch);
+    cudaFree(h->snap);
+    cudaFree(h->partial);
+    cudaFree(h->result);
+    if (h->host_res) cudaFreeHost(h->host_res);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+}
+
+// ------------------------------------------------------------------ kernels
+static void launch_step(clb_handle* h, cudaStream_t s) {
+    const int a = h->par, b = 1 - h->par;
+    const bool sh = h->prm.shift != 0, fo = h->prm.forchheimer != 0;
+    if (sh && fo)
+        k_step_f64<true, true><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
+    else if (sh)
+        k_step_f64<true, false><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
+    else if (fo)
+        k_step_f64<false, true><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
+    else
+        k_step_f64<false, false><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
+    h->par = b;
+}
+
+static void launch_macros(clb_handle* h, double* r, double* u, double* v, double* T) {
+    const int a = h->par;
+    if (h->prm.forchheimer)
+        k_macros_f64<true><<<h->grid, h->block, 0, h->stream>>>(h->f[a], h->g[a], h->coef, h->ayg, h->kp, r, u, v, T);
+    else
+        k_macros_f64<false><<<h->grid, h->block, 0, h->stream>>>(h->f[a], h->g[a], h->coef, h->ayg, h->kp, r, u, v, T);
+}
+
+// Capture kGraphSteps steps starting from buffer parity `par` into an
+// executable graph.  Failure is not an error: steps are then launched one by one.
+static cudaGraphExec_t capture(clb_handle* h, int par) {
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    const int save = h->par;
+    h->par = par;
+    if (cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        h->par = save;
+        cudaGetLastError();
+        return nullptr;
+    }
+    for (int i = 0; i < kGraphSteps; ++i) launch_step(h, h->cap_stream);
+    cudaError_t e = cudaStreamEndCapture(h->cap_stream, &gr);
+    h->par = save;
+    if (e != cudaSuccess || !gr) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) ex = nullptr;
+    cudaGraphDestroy(gr);
+    cudaGetLastError();
+    return ex;
+}
+
+// ------------------------------------------------------------------ API
+static int set_fields_from_scratch(clb_handle* h);
+
+extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi, const double* ay_row,
+                        const clb_bc* bc, void* stream) {
+    if (!out) return fail(nullptr, CLB_ERR_ARG, "clb_init: output handle pointer is NULL");
+    *out = nullptr;
+    if (!p || !phi || !bc) return fail(nullptr, CLB_ERR_ARG, "clb_init: params, phi and bc are required");
+    clb_lattice lat{};
+    std::string why;
+    if (map_params(p, &lat, why) != CLB_OK) return fail(nullptr, CLB_ERR_ARG, "clb_init: %s", why.c_str());
+    for (int s = 0; s < 4; ++s)
+        if (bc->kind[s] != CLB_PERIODIC && bc->kind[s] != CLB_WALL)
+            return fail(nullptr, CLB_ERR_ARG, "clb_init: side %d has an unknown kind", s);
+    if ((bc->kind[CLB_W] == CLB_WALL) != (bc->kind[CLB_E] == CLB_WALL) ||
+        (bc->kind[CLB_S] == CLB_WALL) != (bc->kind[CLB_N] == CLB_WALL))
+        return fail(nullptr, CLB_ERR_ARG, "clb_init: opposite sides must both be periodic or both walls");
+    const int wall_x = bc->kind[CLB_W] == CLB_WALL, wall_y = bc->kind[CLB_S] == CLB_WALL;
+    if ((wall_x && p->nx < 4) || (wall_y && p->ny < 4))
+        return fail(nullptr, CLB_ERR_ARG, "clb_init: a walled direction needs at least 4 nodes");
+    const long long n = (long long)p->nx * p->ny;
+    for (long long i = 0; i < n; ++i)
+        if (!(phi[i] > 0.0 && phi[i] <= 1.0))
+            return fail(nullptr, CLB_ERR_ARG, "clb_init: porosity %g at node %lld is outside (0, 1]", phi[i], i);
+    if (ay_row)
+        for (int y = 0; y < p->ny; ++y)
+            if (!std::isfinite(ay_row[y])) return fail(nullptr, CLB_ERR_ARG, "clb_init: ay_row[%d] is not finite", y);
+
+    clb_handle* h = new (std::nothrow) clb_handle();
+    if (!h) return fail(nullptr, CLB_ERR_OOM, "clb_init: out of host memory");
+    h->prm = *p;
+    h->bc = *bc;
+    h->lat = lat;
+    h->stream = (cudaStream_t)stream;
+    auto bail = [&](int code) {
+        g_init_error = h->err;
+        free_all(h);
+        delete h;
+        return code;
+    };
+#define CKI(call)                                                                                 \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            fail(h, e_ == cudaErrorMemoryAllocation ? CLB_ERR_OOM : CLB_ERR_CUDA, "%s failed: %s", \
+                 #call, cudaGetErrorString(e_));                                                  \
+            return bail(e_ == cudaErrorMemoryAllocation ? CLB_ERR_OOM : CLB_ERR_CUDA);           \
+        }                                                                                         \
+    } while (0)
+    CKI(cudaGetDevice(&h->device));
+    CKI(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+
+    const int px = (p->nx + 31) / 32 * 32;
+    h->lat.pitch = px;
+    KParams& K = h->kp;
+    K.g.nx = p->nx;
+    K.g.ny = p->ny;
+    K.g.px = px;
+    K.g.plane = (long long)px * p->ny;
+    K.g.wall_x = wall_x;
+    K.g.wall_y = wall_y;
+    for (int s = 0; s < 4; ++s) {
+        K.b.uw[s] = bc->u[s];
+        K.b.vw[s] = bc->v[s];
+        K.b.Tw[s] = bc->T[s];
+        K.b.iso[s] = bc->thermal[s] == CLB_ISOTHERMAL;
+    }
+    K.p.ax = p->ax;
+    K.p.gbeta = lat.gbeta;
+    K.p.inv_sigma = 1.0 / p->sigma;
+    K.p.cT2 = 0.5 * p->varpi;
+    K.p.sv = lat.sv;
+    K.p.sp = 0.5 * (lat.sb + lat.sv);
+    K.p.sm = 0.5 * (lat.sb - lat.sv);
+    K.p.s3 = p->s3;
+    K.p.s4 = p->s4;
+    K.p.om_a = 1.0 - lat.zeta_a;
+    K.p.c6 = (1.0 - 0.5 * p->s3) / 3.0;
+    K.p.ca = 1.0 - 0.5 * lat.sv;
+    K.p.cb8 = 1.0 - 0.5 * p->s4;
+    pick_launch(h);
+
+    const size_t fbytes = (size_t)K.g.plane * 9 * sizeof(double);
+    const size_t gbytes = (size_t)K.g.plane * 5 * sizeof(double);
+    for (int i = 0; i < 2; ++i) {
+        CKI(cudaMalloc(&h->f[i], fbytes));
+        CKI(cudaMalloc(&h->g[i], gbytes));
+        // the pitch padding is never read by the kernels; clear it once
+        CKI(cudaMemsetAsync(h->f[i], 0, fbytes, h->stream));
+        CKI(cudaMemsetAsync(h->g[i], 0, gbytes, h->stream));
+    }
+    CKI(cudaMalloc(&h->coef, (size_t)n * sizeof(Coef)));
+    CKI(cudaMalloc(&h->ayg, (size_t)p->ny * sizeof(double)));
+    CKI(cudaMalloc(&h->scratch, (size_t)n * 4 * sizeof(double)));
+    CKI(cudaMalloc(&h->snap, (size_t)n * 3 * sizeof(double)));
+    h->n_partial = reduce_partials(p->nx, p->ny);
+    CKI(cudaMalloc(&h->partial, (size_t)h->n_partial * 4 * sizeof(double)));
+    CKI(cudaMalloc(&h->result, 8 * sizeof(double)));
+    CKI(cudaMallocHost(&h->host_res, 8 * sizeof(double)));
+
+    // per-node constants from phi (staged through the scratch buffer)
+    CKI(cudaMemcpyAsync(h->scratch, phi, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    k_coef<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, h->coef, n, lat.nu, lat.K,
+                                                                 p->forchheimer);
+    CKI(cudaGetLastError());
+    // a_y per row with g beta T0 folded in: G_y = g beta T + (a_y - g beta T0)
+    std::vector<double> ay(p->ny);
+    for (int y = 0; y < p->ny; ++y) ay[y] = (ay_row ? ay_row[y] : p->ay) - lat.gbeta * p->T0;
+    CKI(cudaMemcpyAsync(h->ayg, ay.data(), ay.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CKI(cudaStreamSynchronize(h->stream));
+
+    // start at rest: rho = 1, u = 0, T = T_init, filled on the device
+    k_fill4<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, n, 1.0, 0.0, 0.0, p->T_init);
+    CKI(cudaGetLastError());
+    int rc = set_fields_from_scratch(h);
+    if (rc != CLB_OK) return bail(rc);
+#undef CKI
+    *out = h;
+    return CLB_OK;
+}
+
+extern "C" int clb_set_fields(clb_handle* h, const double* rho, const double* ux, const double* uy,
+                              const double* T) {
+    if (!h) return CLB_ERR_ARG;
+    if (!rho || !T) return fail(h, CLB_ERR_ARG, "clb_set_fields: rho and T are required");
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    for (long long i = 0; i < n; ++i)
+        if (!std::isfinite(rho[i]) || !(rho[i] > 0) || !std::isfinite(T[i]) || (ux && !std::isfinite(ux[i])) ||
+            (uy && !std::isfinite(uy[i])))
+            return fail(h, CLB_ERR_ARG, "clb_set_fields: invalid value at node %lld", i);
+    const size_t b = (size_t)n * sizeof(double);
+    double* d = h->scratch;
+    CK(h, cudaMemcpyAsync(d, rho, b, cudaMemcpyHostToDevice, h->stream));
+    if (ux) CK(h, cudaMemcpyAsync(d + n, ux, b, cudaMemcpyHostToDevice, h->stream));
+    else CK(h, cudaMemsetAsync(d + n, 0, b, h->stream));
+    if (uy) CK(h, cudaMemcpyAsync(d + 2 * n, uy, b, cudaMemcpyHostToDevice, h->stream));
+    else CK(h, cudaMemsetAsync(d + 2 * n, 0, b, h->stream));
+    CK(h, cudaMemcpyAsync(d + 3 * n, T, b, cudaMemcpyHostToDevice, h->stream));
+    return set_fields_from_scratch(h);
+}
+
+// Equilibrium state from the four dense fields (rho, ux, uy, T) held in the
+// scratch buffer; resets the step counter and the residual reference.
+static int set_fields_from_scratch(clb_handle* h) {
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    double* d = h->scratch;
+    h->par = 0;
+    k_set_fields_f64<<<h->grid, h->block, 0, h->stream>>>(h->f[0], h->g[0], h->coef, d, d + n, d + 2 * n,
+                                                         d + 3 * n, h->prm.sigma, h->kp);
+    CK(h, cudaGetLastError());
+    h->t = 0;
+    // residual reference = the new state
+    launch_macros(h, nullptr, h->snap, h->snap + n, h->snap + 2 * n);
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CLB_OK;
+}
+
+extern "C" int clb_step(clb_handle* h, int64_t n) {
+    if (!h) return CLB_ERR_ARG;
+    if (n < 0) return fail(h, CLB_ERR_ARG, "clb_step: negative step count");
+    int64_t left = n;
+    while (left > 0) {
+        if (left >= kGraphSteps && !h->graph_failed) {
+            if (!h->graph[h->par]) {
+                h->graph[h->par] = capture(h, h->par);
+                if (!h->graph[h->par]) {
+                    h->graph_failed = true;
+                    continue;
+                }
+            }
+            CK(h, cudaGraphLaunch(h->graph[h->par], h->stream));   // even count: parity unchanged
+            left -= kGraphSteps;
+        } else {
+            launch_step(h, h->stream);
+            CK(h, cudaGetLastError());
+            left -= 1;
+        }
+    }
+    h->t += n;
+    return CLB_OK;
+}
+
+extern "C" int clb_macros_device(clb_handle* h, double* rho, double* ux, double* uy, double* T) {
+    if (!h) return CLB_ERR_ARG;
+    launch_macros(h, rho, ux, uy, T);
+    CK(h, cudaGetLastError());
+    return CLB_OK;
+}
+
+extern "C" int clb_macros(clb_handle* h, double* rho, double* ux, double* uy, double* T) {
+    if (!h) return CLB_ERR_ARG;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    double* d = h->scratch;
+    launch_macros(h, d, d + n, d + 2 * n, d + 3 * n);
+    CK(h, cudaGetLastError());
+    double* outs[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        if (outs[k])
+            CK(h, cudaMemcpyAsync(outs[k], d + k * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int k = 0; k < 4; ++k)
+        if (outs[k])
+            for (long long i = 0; i < n; ++i)
+                if (!std::isfinite(outs[k][i]))
+                    return fail(h, CLB_ERR_UNSTABLE, "clb_macros: non-finite value at node %lld", i);
+    return CLB_OK;
+}
+
+extern "C" int clb_nusselt(clb_handle* h, int32_t side, double* nu) {
+    if (!h || !nu) return CLB_ERR_ARG;
+    if (side < 0 || side > 3) return fail(h, CLB_ERR_ARG, "clb_nusselt: side must be 0..3");
+    const bool along_y = side == CLB_W || side == CLB_E;
+    const int len = along_y ? h->prm.ny : h->prm.nx;
+    const int depth = along_y ? h->prm.nx : h->prm.ny;
+    if (len < 2 || depth < 3) return fail(h, CLB_ERR_ARG, "clb_nusselt: grid too small");
+    const int nb = (len + kRedThreads - 1) / kRedThreads;
+    if (nb > h->n_partial) return fail(h, CLB_ERR_ARG, "clb_nusselt: too many partials");
+    const int a = h->par;
+    const double scale = -h->lat.L / h->prm.dT / (double)(len - 1);
+    k_nusselt_partial<<<nb, kRedThreads, 0, h->stream>>>(h->g[a], h->coef, h->kp, side, scale, h->partial);
+    k_sum_partials<<<1, kRedThreads, 0, h->stream>>>(h->partial, nb, 1, h->result);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(h->host_res, h->result, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    *nu = h->host_res[0];
+    if (!std::isfinite(*nu)) return fail(h, CLB_ERR_UNSTABLE, "clb_nusselt: non-finite result");
+    return CLB_OK;
+}
+
+extern "C" int clb_residual(clb_handle* h, double* r_u, double* r_T) {
+    if (!h) return CLB_ERR_ARG;
+    const long long n = (long long)h->prm.nx * h->prm.ny;
+    const int nb = (int)((n + kRedThreads - 1) / kRedThreads);
+    const int a = h->par;
+    double* d = h->scratch;
+    // current macros into scratch, then compare with the snapshot and replace it
+    launch_macros(h, nullptr, d, d + n, d + 2 * n);
+    const int nbr = nb < h->n_partial ? nb : h->n_partial;
+    k_residual_partial<<<nbr, kRedThreads, 0, h->stream>>>(d, h->snap, n, h->partial, nbr);
+    k_sum_partials<<<1, kRedThreads, 0, h->stream>>>(h->partial, nbr, 4, h->result);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(h->host_res, h->result, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    (void)a;
+    const double du = h->host_res[0], uu = h->host_res[1], dt = h->host_res[2], tt = h->host_res[3];
+    if (!std::isfinite(du) || !std::isfinite(uu) || !std::isfinite(dt) || !std::isfinite(tt))
+        return fail(h, CLB_ERR_UNSTABLE, "clb_residual: non-finite fields");
+    if (r_u) *r_u = uu > 0 ? std::sqrt(du) / std::sqrt(uu) : std::sqrt(du);
+    if (r_T) *r_T = tt > 0 ? std::sqrt(dt) / std::sqrt(tt) : std::sqrt(dt);
+    return CLB_OK;
+}
+
+extern "C" int64_t clb_time(const clb_handle* h) { return h ? h->t : -1; }
+
+extern "C" int clb_lattice_params(const clb_handle* h, clb_lattice* out) {
+    if (!h || !out) return CLB_ERR_ARG;
+    *out = h->lat;
+    return CLB_OK;
+}
+
+// Checkpoint layout: 8 int64 header words (magic, version, nx, ny,
+// precision, t, 0, 0), then f (9 planes) and g (5 planes), each plane ny*nx
+// doubles without pitch padding.
+static const int64_t kMagic = 0x434c42314750554cLL;
+
+extern "C" size_t clb_state_bytes(const clb_handle* h) {
+    if (!h) return 0;
+    return 8 * sizeof(int64_t) + (size_t)14 * h->prm.nx * h->prm.ny * sizeof(double);
+}
+
+extern "C" int clb_get_state(clb_handle* h, void* buf, size_t bytes) {
+    if (!h || !buf) return CLB_ERR_ARG;
+    if (bytes < clb_state_bytes(h)) return fail(h, CLB_ERR_ARG, "clb_get_state: buffer too small");
+    int64_t* hd = (int64_t*)buf;
+    int64_t hdr[8] = {kMagic, 1, h->prm.nx, h->prm.ny, h->prm.precision, h->t, 0, 0};
+    std::memcpy(hd, hdr, sizeof hdr);
+    char* p = (char*)buf + sizeof hdr;
+    const size_t row = (size_t)h->prm.nx * sizeof(double), pitch = (size_t)h->kp.g.px * sizeof(double);
+    const size_t plane = row * h->prm.ny;
+    for (int i = 0; i < 14; ++i) {
+        const double* src = i < 9 ? h->f[h->par] + i * h->kp.g.plane : h->g[h->par] + (i - 9) * h->kp.g.plane;
+        CK(h, cudaMemcpy2DAsync(p + i * plane, row, src, pitch, row, h->prm.ny, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CLB_OK;
+}
+
+extern "C" int clb_set_state(clb_handle* h, const void* buf, size_t bytes) {
+    if (!h || !buf) return CLB_ERR_ARG;
+    if (bytes < clb_state_bytes(h)) return fail(h, CLB_ERR_STATE, "clb_set_state: buffer too small");
+    int64_t hdr[8];
+    std::memcpy(hdr, buf, sizeof hdr);
+    if (hdr[0] != kMagic || hdr[1] != 1 || hdr[2] != h->prm.nx || hdr[3] != h->prm.ny ||
+        hdr[4] != h->prm.precision)
+        return fail(h, CLB_ERR_STATE, "clb_set_state: checkpoint does not match this simulation");
+    const char* p = (const char*)buf + sizeof hdr;
+    const size_t row = (size_t)h->prm.nx * sizeof(double), pitch = (size_t)h->kp.g.px * sizeof(double);
+    const size_t plane = row * h->prm.ny;
+    h->par = 0;
+    for (int i = 0; i < 14; ++i) {
+        double* dst = i < 9 ? h->f[0] + i * h->kp.g.plane : h->g[0] + (i - 9) * h->kp.g.plane;
+        CK(h, cudaMemcpy2DAsync(dst, pitch, p + i * plane, row, row, h->prm.ny, cudaMemcpyHostToDevice, h->stream));
+    }
+    h->t = hdr[5];
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CLB_OK;
+}
+
+extern "C" int clb_sync(clb_handle* h) {
+    if (!h) return CLB_ERR_ARG;
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CLB_OK;
+}
+
+extern "C" void clb_destroy(clb_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+extern "C" const char* clb_last_error(const clb_handle* h) {
+    return h ? h->err.c_str() : g_init_error.c_str();
+}

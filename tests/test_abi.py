@@ -1,0 +1,59 @@
+"""The C ABI library builds for sm_103a, loads without a GPU, and exports
+every entry point include/clb.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "clb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(clb_[a-z_]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("clb_init", "clb_step", "clb_macros", "clb_nusselt", "clb_residual", "clb_destroy",
+              "clb_get_state", "clb_set_state", "clb_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_2110_05943_gb300 import clb
+    lib = clb.load()
+    missing = [n for n in _declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_params_default_and_abi_struct_sizes():
+    from paper_2110_05943_gb300 import clb
+    p = clb.clb_params_default()
+    assert (p.nx, p.ny) == (64, 64) and p.Ra == 1e4 and p.s3 == 1.2 and p.s4 == 1.8 and p.Ma == 0.1
+    assert ctypes.sizeof(clb.ClbParams) == 6 * 4 + 18 * 8
+    bc = clb.clb_bc_cavity(1.0, 0.0)
+    assert list(bc.kind) == [1, 1, 1, 1] and list(bc.thermal) == [1, 1, 0, 0]
+
+
+def test_init_rejects_bad_arguments_before_touching_the_gpu():
+    """Argument validation happens on the host first; these calls fail with
+    CLB_ERR_ARG whether or not a GPU is present."""
+    import numpy as np
+    import pytest
+    from paper_2110_05943_gb300 import clb
+    bc = clb.clb_bc_cavity()
+    p = clb.clb_params_default(nx=16, ny=16)
+    with pytest.raises(clb.ClbError) as e:
+        clb.clb_init(p, np.full(256, 1.5), bc)        # porosity > 1
+    assert e.value.code == clb.CLB_ERR_ARG
+    with pytest.raises(clb.ClbError):
+        clb.clb_init(clb.clb_params_default(nx=3, ny=16), np.full(48, 0.5), bc)   # walled dim < 4
+    with pytest.raises(clb.ClbError):
+        clb.clb_init(clb.clb_params_default(nx=16, ny=16, Da=-1.0), np.full(256, 0.5), bc)
+    with pytest.raises(clb.ClbError):
+        clb.clb_init(clb.clb_params_default(nx=16, ny=16, Ra=0.0), np.full(256, 0.5), bc)  # Eq. 46 needs Ra
+    mixed = clb.clb_bc(("wall", "periodic", "wall", "wall"))
+    with pytest.raises(clb.ClbError):
+        clb.clb_init(p, np.full(256, 0.5), mixed)

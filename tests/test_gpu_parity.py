@@ -1,0 +1,195 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Bar (FP64 form): max_x |gpu - oracle| / max_x |oracle| <= 1e-10 for rho - 1,
+u_x, u_y and T after the stated number of steps.  The two sides differ only
+in rounding order (the kernel contracts to FMA and uses the delta form of
+the collision; the oracle multiplies dense matrices without contraction),
+so the measured gap is ~1e-13 and the bound leaves three decades.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from cases import CAVITY, CHANNEL_X, PERIODIC, build, field_errors, rel_err
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.init()
+
+
+def _check(orc, sim, tol=TOL):
+    errs = field_errors(sim.macros(), orc.macros())
+    assert all(e <= tol for e in errs.values()), errs
+    return errs
+
+
+def test_parity_cavity_64_uniform_10k_steps():
+    """The 64^2 porous cavity (phi 0.6, Da 1e-2, Ra 1e4, Pr 1, sigma 1):
+    10,000 steps, all four fields within 1e-10 of the oracle."""
+    orc, sim = build(64, 64, 0.6, Ra=1e4, Da=1e-2, Pr=1.0)
+    orc.step(10_000)
+    sim.step(10_000)
+    _check(orc, sim)
+    assert sim.time == 10_000
+    nu_g, nu_o = sim.nusselt(0), orc.nusselt(0)
+    assert abs(nu_g - nu_o) <= 1e-10 * abs(nu_o)
+
+
+def test_parity_random_porosity_ragged_grid():
+    """Seeded Gaussian-random-field porosity, non-square grid with a ragged
+    tile tail in x (300 = 2 x 128 + 44), Forchheimer on, sigma 0.8."""
+    from paper_2110_05943_gb300.inputs import porosity_field
+    nx, ny = 300, 37
+    phi = porosity_field(nx, ny, seed=11, ell=8.0)
+    orc, sim = build(nx, ny, phi, Ra=1e6, Da=1e-3, Pr=0.71, sigma=0.8)
+    orc.step(1500)
+    sim.step(1500)
+    _check(orc, sim)
+
+
+@pytest.mark.parametrize("shift,forch", [(False, True), (True, False), (False, False)])
+def test_parity_variants(shift, forch):
+    """Unit shift (the MRT limit of Sec. 2) and the Brinkman-Darcy model
+    (F_phi = 0), on a cavity with varying porosity."""
+    from paper_2110_05943_gb300.inputs import porosity_field
+    n = 40
+    phi = porosity_field(n, n, seed=2, ell=6.0)
+    orc, sim = build(n, n, phi, Ra=1e5, Da=1e-2, Pr=0.71, shift=shift, forchheimer=forch)
+    orc.step(2000)
+    sim.step(2000)
+    _check(orc, sim)
+
+
+def test_parity_mixed_convection_channel():
+    """Sec. 3.1 channel: periodic in x, moving hot top wall, injection
+    through the bottom, y-dependent external force of Eq. 42."""
+    nx, ny = 37, 33
+    H, u1, Re = ny - 1, 0.01, 5.0
+    nu = H * u1 / Re
+    import oracle
+    p = oracle.Problem(nx=nx, ny=ny, Ra=100.0, Da=0.01, nu=nu, forchheimer=False)
+    lat = oracle.lattice_params(p)
+    y = np.arange(ny, dtype=float)
+    ay = lat.nu / lat.K * u1 - lat.gbeta * (np.exp(y * u1 / lat.alpha_e) - 1) / (np.exp(H * u1 / lat.alpha_e) - 1)
+    orc, sim = build(nx, ny, 0.6, Ra=100.0, Da=0.01, nu=nu, forchheimer=False, kind=CHANNEL_X,
+                     u=(0, 0, 0.0, u1), v=(0, 0, u1, u1), T=(None, None, 0.0, 1.0), ay_row=ay)
+    orc.step(3000)
+    sim.step(3000)
+    _check(orc, sim)
+
+
+@pytest.mark.parametrize("shift", [True, False])
+def test_parity_periodic_from_random_fields(shift):
+    """Fully periodic domain started from smooth random (rho, u, T) fields
+    (exercises set_fields and the periodic wrap on both axes)."""
+    from paper_2110_05943_gb300.inputs import porosity_field, smooth_fields
+    nx, ny = 50, 40
+    phi = porosity_field(nx, ny, seed=4, ell=5.0)
+    rho, ux, uy, T = smooth_fields(nx, ny, seed=9)
+    orc, sim = build(nx, ny, phi, Ra=1e5, Da=1e-2, Pr=0.71, sigma=1.3, L=32, shift=shift, kind=PERIODIC,
+                     T=(None,) * 4)
+    orc.set_fields(rho.ravel(), ux.ravel(), uy.ravel(), T.ravel())
+    sim.set_fields(rho, ux, uy, T)
+    _check(orc, sim, tol=1e-13)       # at t = 0 both are the same equilibria
+    orc.step(1000)
+    sim.step(1000)
+    _check(orc, sim)
+
+
+def test_parity_small_and_odd_grids():
+    """Smallest walled grid (4 x 4), and a 5 x 33 cavity: every node is at or
+    next to a wall; exercises corners and the adiabatic extrapolation."""
+    for nx, ny in ((4, 4), (5, 33), (33, 5)):
+        orc, sim = build(nx, ny, 0.7, Ra=1e4, Da=1e-2)
+        orc.step(300)
+        sim.step(300)
+        _check(orc, sim)
+
+
+def test_nusselt_matches_oracle_on_all_walls():
+    orc, sim = build(48, 40, 0.6, Ra=1e5, Da=1e-2, Pr=0.71)
+    orc.step(3000)
+    sim.step(3000)
+    import oracle
+    _, _, _, T = orc.macros()
+    for side in range(4):
+        want = oracle.nusselt(T, side, orc.lat.L)
+        got = sim.nusselt(side)
+        assert abs(got - want) <= 1e-10 * max(1.0, abs(want)), (side, got, want)
+
+
+def test_residual_matches_definition():
+    """clb_residual = ||u^n - u^m|| / ||u^n|| (and the same for T) against
+    the fields at the previous call."""
+    orc, sim = build(32, 32, 0.6, Ra=1e4, Da=1e-2)
+    orc.step(500)
+    sim.step(500)
+    ru, _ = sim.residual()          # reference was the state at rest: ratio exactly 1
+    assert abs(ru - 1.0) < 1e-12
+    _, ux0, uy0, T0 = orc.macros()
+    orc.step(100)
+    sim.step(100)
+    _, ux1, uy1, T1 = orc.macros()
+    ru, rT = sim.residual()
+    want_u = math.sqrt(np.sum((ux1 - ux0) ** 2 + (uy1 - uy0) ** 2)) / math.sqrt(np.sum(ux1 ** 2 + uy1 ** 2))
+    want_T = math.sqrt(np.sum((T1 - T0) ** 2)) / math.sqrt(np.sum(T1 ** 2))
+    assert abs(ru / want_u - 1) < 1e-8 and abs(rT / want_T - 1) < 1e-8
+
+
+def test_checkpoint_resume_is_bit_identical():
+    _, sim = build(40, 24, 0.5, Ra=1e5, Da=1e-3, with_oracle=False)
+    sim.step(333)
+    st = sim.get_state()
+    sim.step(77)
+    a = sim.macros()
+    sim.set_state(st)
+    assert sim.time == 333
+    sim.step(77)
+    b = sim.macros()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_step_zero_and_graph_parity_across_odd_counts():
+    """Mixed single launches and 32-step graphs give the same state as one
+    long call (the graph path keeps the buffer parity)."""
+    _, s1 = build(20, 20, 0.6, with_oracle=False)
+    _, s2 = build(20, 20, 0.6, with_oracle=False)
+    s1.step(0)
+    s1.step(101)
+    for n in (1, 33, 2, 64, 1):
+        s2.step(n)
+    for x, y in zip(s1.macros(), s2.macros()):
+        assert np.array_equal(x, y)
+
+
+def test_periodic_conservation_gpu():
+    """Sum rho and sum sigma T are invariant on a periodic domain."""
+    from paper_2110_05943_gb300.inputs import smooth_fields
+    nx, ny = 64, 48
+    rho, ux, uy, T = smooth_fields(nx, ny, seed=1)
+    _, sim = build(nx, ny, 0.7, Ra=1e5, Da=1e-2, L=40, sigma=1.5, kind=PERIODIC, T=(None,) * 4,
+                   with_oracle=False)
+    sim.set_fields(rho, ux, uy, T)
+    r0, _, _, T0 = sim.macros()
+    sim.step(5000)
+    r1, _, _, T1 = sim.macros()
+    assert abs(r1.sum() / r0.sum() - 1) < 1e-13
+    assert abs(T1.sum() / T0.sum() - 1) < 1e-13
+
+
+def test_invalid_state_rejected():
+    from paper_2110_05943_gb300 import clb
+    _, a = build(16, 16, 0.6, with_oracle=False)
+    _, b = build(20, 16, 0.6, with_oracle=False)
+    with pytest.raises(clb.ClbError) as e:
+        b.set_state(a.get_state())
+    assert e.value.code == clb.CLB_ERR_STATE
