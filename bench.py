@@ -45,11 +45,16 @@ WORKLOAD = ("{n}x{n} porous cavity, seeded GRF porosity 0.3+0.6*Phi(g) (l=32, se
 # Algorithmic bytes per coupled cell update of the FP64 form: 14 distribution
 # values read and 14 written (8 B each) plus the porosity (8 B).
 BYTES_PER_CCU_F64 = 28 * 8 + 8
-# FP64 floating-point operations per interior coupled cell update executed by
-# k_step_f64 (shift + Forchheimer), from the ncu instruction counters
-# (dadd + dmul + 2 dfma per launch / nodes); see profiles/.
-FP64_FLOP_PER_CCU = None
-SMS, DFMA_PER_CLK_PER_SM = 152, 2   # GB300: 1.25 TFLOP/s FP64 nominal at 2.07 GHz
+# FP64 floating-point operations per coupled cell update executed by
+# k_step_f64<shift, forchheimer> (dadd + dmul + 2 dfma per launch / nodes,
+# ncu instruction counters; profiles/k_step_f64_cavity2048.md), and the FP64
+# pipe instructions (dadd + dmul + dfma) per node.
+FP64_FLOP_PER_CCU = 290.0
+FP64_INST_PER_CCU = 200.7
+# DRAM bytes per launch of k_step_f64 at 4096^2: 246.7 B/node measured by ncu
+# on the 2048^2 case (same kernel), scaled by the node count.
+DRAM_BYTES_PER_CCU_MEASURED = 246.7
+SMS, DFMA_PER_CLK_PER_SM = 152, 2   # GB300 FP64 pipe: 2 DFMA/clk/SM (1.25 TFLOP/s at 2.07 GHz)
 
 
 def _peaks():
@@ -281,10 +286,14 @@ def run_ours(args):
     fp64_peak = SMS * DFMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
     if FP64_FLOP_PER_CCU:
         ach = FP64_FLOP_PER_CCU * cells / per_launch / 1e12
+        inst_rate = FP64_INST_PER_CCU * cells / per_launch
+        inst_peak = SMS * DFMA_PER_CLK_PER_SM * sm_mhz * 1e6
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": None, "kernel": "k_step_f64<shift, forchheimer>",
-                "peak_source": f"FP64 pipe: {SMS} SMs x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 x {sm_mhz:.0f} MHz "
-                               "(median SM clock under load)",
+                "traffic": DRAM_BYTES_PER_CCU_MEASURED * cells if NX == 4096 else None,
+                "kernel": "k_step_f64<shift, forchheimer>", "flop_per_ccu": FP64_FLOP_PER_CCU,
+                "peak_source": f"FP64 pipe: {SMS} SMs x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 flop x {sm_mhz:.0f} MHz "
+                               "(median SM clock in the timed region; FMA probe measured 1.253 TFLOP/s)",
+                "fp64_pipe_frac": inst_rate / inst_peak,
                 "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                         "bytes_per_ccu": BYTES_PER_CCU_F64, "peak_source": f"{src} hbm_gbs"}}
     else:

@@ -193,3 +193,45 @@ def test_invalid_state_rejected():
     with pytest.raises(clb.ClbError) as e:
         b.set_state(a.get_state())
     assert e.value.code == clb.CLB_ERR_STATE
+
+
+def test_full_size_4096_corner_patches_match_oracle():
+    """The 4096^2 seeded-porosity cavity at full size, in the launch
+    configuration bench.py times: after 200 steps every node within 48 of a
+    corner is recomputed by the oracle on a 256^2 sub-domain that carries the
+    true corner walls, the same porosity values and the full grid's lattice
+    parameters (L = 4095).  The sub-domain's two artificial walls perturb it
+    by at most one node per step (front at 255 - 200 = 55 > 47), so the
+    compared region is exact.  (200 steps, not fewer: before that the
+    velocities are ~1e-6 and single roundings already read as 1e-10 of the
+    field maximum.)  The untouched interior must still be exactly at rest."""
+    import oracle
+    from paper_2110_05943_gb300.inputs import porosity_field
+    n, steps, P, keep = 4096, 200, 256, 48
+    phi = porosity_field(n, n, seed=20211012, ell=32.0)
+    case = dict(Ra=1e6, Da=1e-3, Pr=0.71, sigma=1.0)
+    _, sim = build(n, n, phi, with_oracle=False, **case)
+    sim.step(steps)
+    rho, ux, uy, T = sim.macros()
+    assert np.all(ux[1000:3000, 1000:3000] == 0.0) and np.all(uy[1000:3000, 1000:3000] == 0.0)
+    assert np.all(T[1000:3000, 1000:3000] == 0.5)
+    for cy in (0, 1):
+        for cx in (0, 1):
+            ys = slice(0, P) if cy == 0 else slice(n - P, n)
+            xs = slice(0, P) if cx == 0 else slice(n - P, n)
+            # W/E: the true wall keeps its temperature; the artificial side is isothermal at T_init
+            Tside = (1.0, 0.5) if cx == 0 else (0.5, 0.0)
+            p = oracle.Problem(nx=P, ny=P, L=float(n - 1), walls=oracle.Walls(
+                ("wall",) * 4, (0.0,) * 4, (0.0,) * 4, (Tside[0], Tside[1], None, None)), **case)
+            o = oracle.Oracle(p, phi=np.ascontiguousarray(phi[ys, xs]))
+            o.step(steps)
+            want = o.macros()
+            ry = slice(0, keep) if cy == 0 else slice(P - keep, P)
+            rx = slice(0, keep) if cx == 0 else slice(P - keep, P)
+            got = [a[ys, xs][ry, rx] for a in (rho, ux, uy, T)]
+            ref = [a[ry, rx] for a in want]
+            errs = field_errors(got, ref)
+            assert all(e <= TOL for e in errs.values()), ((cy, cx), errs)
+    # FP64 device reduction over 4096 wall nodes vs the same formula on the host
+    nu_host = oracle.nusselt(T, oracle.W, float(n - 1))
+    assert abs(sim.nusselt(0) - nu_host) <= 1e-12 * abs(nu_host)
