@@ -180,6 +180,39 @@ int clb_sync(clb_handle* h);
 
 void clb_destroy(clb_handle* h);
 
+/* Allocation-free Nusselt reduction.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc -- code that
+ * runs inside another framework's memory pool, which may already hold
+ * nearly all device memory and must see every allocation, and loops where
+ * an allocation's implicit device-wide synchronisation cannot be afforded.
+ *
+ * Computes the same mean Nusselt number as clb_nusselt (Nu = -L dT/dn / dT,
+ * one-sided second-order difference, trapezoid rule along the wall) from a
+ * temperature field the caller already holds on the device.
+ *   T      : device pointer, ny*nx FP64 values, (ny, nx) row-major (for
+ *            instance filled by clb_macros_device); read only
+ *   side   : CLB_W, CLB_E, CLB_S or CLB_N
+ *   L, dT  : characteristic length and temperature difference (> 0)
+ *   nu     : device pointer to one double, written with the result
+ *   stream : cudaStream_t the two kernels run on (NULL: legacy stream)
+ * Asynchronous: nu holds the result once the stream reaches it.
+ * Scratch: a fixed array of CLB_STATIC_MAX_PARTIALS doubles (8 KiB) in the
+ * library's device memory, present on every GPU that loads the library
+ * until the process exits, so walls longer than CLB_STATIC_MAX_WALL nodes
+ * are rejected with CLB_ERR_ARG.  No cudaMalloc, cudaFree or allocating
+ * library routine is called.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  All calls share the one array:
+ * calls whose kernels can overlap on the GPU (different streams without
+ * ordering between them) race and give wrong results.  Every slot a call
+ * reads it has written itself, so nothing needs clearing between calls.
+ * Errors: CLB_ERR_ARG (bad pointer, side or size), CLB_ERR_CUDA; message
+ * in clb_last_error(NULL). */
+#define CLB_STATIC_MAX_PARTIALS 1024
+#define CLB_STATIC_MAX_WALL (CLB_STATIC_MAX_PARTIALS * 256)
+int clb_nusselt_field_static(const double* T, int32_t nx, int32_t ny, int32_t side, double L, double dT,
+                             double* nu, void* stream);
+
 /* Last error message of h, or of the calling thread's last failed
  * clb_init when h is NULL. */
 const char* clb_last_error(const clb_handle* h);

@@ -1,7 +1,8 @@
 """Build the CUDA library libclb.so in-tree for sm_103a (GB300).
 
-One translation unit (csrc/clb_api.cu includes the kernel headers), one
--gencode, no cmake: a few seconds on either machine.
+Two translation units (csrc/clb_api.cu includes the kernel headers;
+csrc/clb_static.cu is the allocation-free reduction), one -gencode, no
+cmake: a few seconds on either machine.
 """
 from __future__ import annotations
 
@@ -14,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libclb.so")
-SOURCES = ["clb_api.cu"]
+SOURCES = ["clb_api.cu", "clb_static.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

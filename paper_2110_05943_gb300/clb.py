@@ -89,7 +89,9 @@ def load(build_if_needed: bool = True):
     L.clb_destroy.restype = None
     L.clb_last_error.argtypes = [_VP]
     L.clb_last_error.restype = ctypes.c_char_p
-    for name in ("clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
+    L.clb_nusselt_field_static.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
+                                           ctypes.c_double, _VP, _VP]
+    for name in ("clb_nusselt_field_static", "clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
                  "clb_residual", "clb_lattice_params", "clb_get_state", "clb_set_state", "clb_sync"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -192,6 +194,16 @@ def clb_nusselt(h, side: int) -> float:
     v = ctypes.c_double()
     _check(load().clb_nusselt(h, int(side), ctypes.byref(v)), h)
     return v.value
+
+
+def clb_nusselt_field_static(T_ptr: int, nx: int, ny: int, side: int, L: float, dT: float, nu_ptr: int,
+                             stream=None):
+    """Allocation-free Nusselt reduction over a device temperature field
+    (device pointers as ints); the result lands in the device double at
+    nu_ptr, asynchronously on `stream`."""
+    rc = load().clb_nusselt_field_static(T_ptr, int(nx), int(ny), int(side), float(L), float(dT), nu_ptr,
+                                         _VP(stream) if stream else None)
+    _check(rc, None)
 
 
 def clb_residual(h):

@@ -565,6 +565,9 @@ extern "C" void clb_destroy(clb_handle* h) {
     delete h;
 }
 
+// Message for clb_last_error(NULL) from entry points without a handle.
+void clb_internal_set_error(const char* msg) { g_init_error = msg ? msg : ""; }
+
 extern "C" const char* clb_last_error(const clb_handle* h) {
     return h ? h->err.c_str() : g_init_error.c_str();
 }
