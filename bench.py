@@ -49,8 +49,8 @@ BYTES_PER_CCU_F64 = 28 * 8 + 8
 # k_step_f64<shift, forchheimer> (dadd + dmul + 2 dfma per launch / nodes,
 # ncu instruction counters; profiles/k_step_f64_cavity2048.md), and the FP64
 # pipe instructions (dadd + dmul + dfma) per node.
-FP64_FLOP_PER_CCU = 290.0
-FP64_INST_PER_CCU = 200.7
+FP64_FLOP_PER_CCU = 289.5
+FP64_INST_PER_CCU = 200.4
 # DRAM bytes per launch of k_step_f64 at 4096^2: 246.7 B/node measured by ncu
 # on the 2048^2 case (same kernel), scaled by the node count.
 DRAM_BYTES_PER_CCU_MEASURED = 246.7
