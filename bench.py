@@ -197,6 +197,44 @@ def steady_state_64(clb, torch):
             "nu_at_20000_steps": nu20k}
 
 
+FORMS = {  # storage form -> (precision code, algorithmic bytes per coupled cell update)
+    "f16n": (2, 28 * 2 + 2 * 8 + 4),   # 14 FP16 deviations read+written, 8 B record read+written, FP32 1/phi
+    "f16s": (1, 28 * 2 + 4),           # 14 FP16 deviations read+written, FP32 phi
+}
+
+
+def reduced_precision_forms(clb, torch, args, hbm_peak, src):
+    """Throughput of the FP16-storage forms on the 8192^2 seeded cavity
+    (Da 1e-3, Ra 1e6, Pr 0.71, sigma 0.8), CUDA events over the timed steps."""
+    from paper_2110_05943_gb300.inputs import porosity_field
+    n = 8192
+    phi = porosity_field(n, n, seed=PHI_SEED, ell=PHI_ELL)
+    out = {}
+    stream = torch.cuda.current_stream()
+    for name, (prec, bpn) in FORMS.items():
+        p = clb.clb_params_default(nx=n, ny=n, Ra=1e6, Da=1e-3, Pr=0.71, sigma=0.8, precision=prec)
+        sim = clb.Simulation.create(p, phi, clb.clb_bc_cavity(1.0, 0.0), stream=stream.cuda_stream)
+        sim.step(args.warmup)
+        torch.cuda.synchronize()
+        steps = max(args.steps, 64)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        sim.close()
+        gbs = bpn * n * n / (t / steps) / 1e9
+        out[name] = {"workload": f"{n}x{n} porous cavity, seeded GRF porosity, Da 1e-3, Ra 1e6, Pr 0.71, sigma 0.8",
+                     "value": n * n * steps / t / 1e6, "unit": UNIT, "steps": steps, "ms_per_step": t / steps * 1e3,
+                     "dtype": "f32 arithmetic, f16 storage",
+                     "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": gbs / hbm_peak, "bytes_per_ccu": bpn, "traffic": None,
+                                  "kernel": f"k_step<StoreH16{'N' if name == 'f16n' else ''}>",
+                                  "peak_source": f"{src} hbm_gbs"}}
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -218,7 +256,8 @@ def run_ours(args):
     clb.load()
     phi = _porosity()
     stream = torch.cuda.current_stream()
-    p = clb.clb_params_default(nx=NX, ny=NY, **CASE)
+    prec = {"f64": 0, "f16s": 1, "f16n": 2}[args.precision]
+    p = clb.clb_params_default(nx=NX, ny=NY, precision=prec, **CASE)
     sim = clb.Simulation.create(p, phi, clb.clb_bc_cavity(1.0, 0.0), stream=stream.cuda_stream)
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -284,7 +323,13 @@ def run_ours(args):
     gbs = BYTES_PER_CCU_F64 * cells / per_launch / 1e9
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     fp64_peak = SMS * DFMA_PER_CLK_PER_SM * 2 * sm_mhz * 1e6 / 1e12
-    if FP64_FLOP_PER_CCU:
+    if args.precision != "f64":
+        bpn = FORMS[args.precision][1]
+        gb = bpn * cells / per_launch / 1e9
+        roof = {"bound": "hbm", "achieved": gb, "peak": hbm_peak, "unit": "GB/s", "frac": gb / hbm_peak,
+                "traffic": None, "kernel": f"k_step<{args.precision}>", "bytes_per_ccu": bpn,
+                "peak_source": f"{src} hbm_gbs"}
+    elif FP64_FLOP_PER_CCU:
         ach = FP64_FLOP_PER_CCU * cells / per_launch / 1e12
         inst_rate = FP64_INST_PER_CCU * cells / per_launch
         inst_peak = SMS * DFMA_PER_CLK_PER_SM * sm_mhz * 1e6
@@ -302,12 +347,15 @@ def run_ours(args):
                 "peak_source": f"{src} hbm_gbs"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(n=NX), "nx": NX, "ny": NY, "cells": cells, "replicas": ws,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "f64" else "f32 arithmetic, f16 storage", "data": "synthetic",
+            "config": {"workload": WORKLOAD.format(n=NX).replace("FP64", args.precision.upper()), "nx": NX, "ny": NY, "cells": cells, "replicas": ws,
                        "l2": f"state {NX * NY * 14 * 16 / 1e9:.2f} GB per replica (two buffers) vs 0.13 GB L2: no flush",
                        "parallelism": f"replicas x{ws}", "nu_hot_wall_after": nu},
             "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
             "e2e": e2e}
+    if not args.no_forms:
+        line["forms"] = reduced_precision_forms(clb, torch, args, hbm_peak, src)
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(phi)
     if not args.no_steady:
@@ -324,7 +372,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-steady", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the FP16-storage forms at 8192^2")
     ap.add_argument("--size", type=int, default=4096, help="grid side (default 4096; smaller for profiling)")
+    ap.add_argument("--precision", choices=("f64", "f16s", "f16n"), default="f64",
+                    help="storage form of the main measurement (default f64, the reported workload)")
     args = ap.parse_args()
     global NX, NY
     NX = NY = args.size

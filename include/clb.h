@@ -47,8 +47,19 @@ extern "C" {
 enum { CLB_W = 0, CLB_E = 1, CLB_S = 2, CLB_N = 3 };
 enum { CLB_PERIODIC = 0, CLB_WALL = 1 };
 enum { CLB_ADIABATIC = 0, CLB_ISOTHERMAL = 1 };
-/* Arithmetic / storage form of the distributions. */
-enum { CLB_F64 = 0 };
+/* Arithmetic / storage form of the distributions (reductions stay FP64).
+ *   CLB_F64  : FP64 storage and arithmetic; 232 B per node update.
+ *   CLB_F16S : each distribution stored in FP16 as its deviation from the
+ *              rest state (w_i rho_0 for f, the D2Q5 equilibrium at u = 0,
+ *              T = T0 for g), arithmetic in FP32; 60 B per node update.
+ *              The rest population's deviation is O(dT), so T is quantised
+ *              at ~2e-4 dT every step: fine for transients, not for
+ *              converged Nusselt numbers.
+ *   CLB_F16N : each post-collision value stored in FP16 as its deviation
+ *              from the local equilibrium of the node that wrote it, plus
+ *              that node's (rho - 1, u, T - T0) in FP16 as the baseline;
+ *              FP32 arithmetic; 76 B per node update. */
+enum { CLB_F64 = 0, CLB_F16S = 1, CLB_F16N = 2 };
 
 /* Boundary specification.  Opposite sides must both be periodic or both
  * walls; a walled direction needs at least 4 nodes.  Wall nodes lie on the
@@ -85,7 +96,7 @@ typedef struct {
  *   forchheimer : 1 = Ergun F_phi of Eq. 5, 0 = F_phi = 0
  *   shift : 1 = porous shift matrices (Eqs. 14, 31); 0 = unit shifts, the
  *           non-orthogonal MRT limit named at the end of Sec. 2
- *   precision : CLB_F64
+ *   precision : CLB_F64, CLB_F16S or CLB_F16N
  * Fixed by the paper (Sec. 3): s_0 = s_1 = 1, zeta_T = zeta_e = zeta_nu = 1.
  * The permeability is K = Da L^2, uniform; F_phi(phi(x)) and every phi
  * factor are taken at the node. */

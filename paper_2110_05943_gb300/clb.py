@@ -26,6 +26,8 @@ W, E, S, N = 0, 1, 2, 3
 CLB_PERIODIC, CLB_WALL = 0, 1
 CLB_ADIABATIC, CLB_ISOTHERMAL = 0, 1
 CLB_F64 = 0
+CLB_F16S = 1
+CLB_F16N = 2
 
 
 class ClbError(RuntimeError):

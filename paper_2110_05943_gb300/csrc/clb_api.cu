@@ -1,8 +1,9 @@
 // clb_api.cu -- host side of the C ABI declared in include/clb.h.
 //
 // Parameter mapping (Sec. 3 and Eqs. 37, 38, 46 of arXiv:2110.05943),
-// device memory, the CUDA-graph step driver, and the FP64 reductions for the
-// Nusselt number and the steady-state residual.
+// device memory for the two storage forms (FP64, and FP16 deviations from
+// the rest state with FP32 arithmetic), the CUDA-graph step driver, and the
+// FP64 reductions for the Nusselt number and the steady-state residual.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -15,7 +16,7 @@
 #include <vector>
 
 #include "../../include/clb.h"
-#include "clb_f64.cuh"
+#include "clb_kernels.cuh"
 #include "clb_reduce.cuh"
 
 using namespace clb;
@@ -37,17 +38,22 @@ struct clb_handle {
     clb_params prm{};
     clb_bc bc{};
     clb_lattice lat{};
-    KParams kp{};
+    KParamsT<double> k64{};       // FP64 form
+    KParamsT<float> k32{};        // FP16 forms
+    int prec = CLB_F64;
+    size_t es = 8;                // bytes per stored distribution value
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     int device = 0;
-    // distributions, ping-pong: buf[par] holds the post-collision values of
+    // distributions, ping-pong: buffer par holds the post-collision values of
     // the last step; par flips every step
-    double* f[2] = {nullptr, nullptr};
-    double* g[2] = {nullptr, nullptr};
+    void* f[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    uint2* rec[2] = {nullptr, nullptr};   // FP16N form: per-node baseline record
     int par = 0;
-    Coef* coef = nullptr;
-    double* ayg = nullptr;
+    CoefT<double>* coef = nullptr;   // FP64 form: per-node constants
+    float* phi32 = nullptr;          // FP16 forms: porosity (dense) or 1/phi (pitched)
+    void* ayg = nullptr;             // a_y - g beta T0 per row (double or float)
     double* scratch = nullptr;       // 4 dense fields (macros, set_fields)
     double* snap = nullptr;          // 3 dense fields (residual reference)
     double* partial = nullptr;       // block partial sums of the reductions
@@ -59,6 +65,17 @@ struct clb_handle {
     bool graph_failed = false;
     dim3 block, grid;
     std::string err;
+
+    AuxT<double> aux64() const { return AuxT<double>{coef, nullptr, nullptr, (const double*)ayg}; }
+    AuxT<float> aux32() const {
+        return prec == CLB_F16N ? AuxT<float>{nullptr, nullptr, phi32, (const float*)ayg}
+                                : AuxT<float>{nullptr, phi32, nullptr, (const float*)ayg};
+    }
+    template <typename S>
+    BufT<S> buf(int i) const { return BufT<S>{(S*)f[i], (S*)g[i], rec[i]}; }
+    const Geo& geo() const { return k64.g; }
+    // bytes per node of one stored state (distributions + record)
+    size_t node_bytes() const { return 14 * es + (prec == CLB_F16N ? sizeof(uint2) : 0); }
 };
 
 static int fail(clb_handle* h, int code, const char* fmt, ...) {
@@ -129,7 +146,8 @@ static int map_params(const clb_params* p, clb_lattice* lat, std::string& why) {
     char buf[256];
     auto bad = [&](const char* m) { why = m; return CLB_ERR_ARG; };
     if (p->nx < 1 || p->ny < 1) return bad("nx and ny must be positive");
-    if (p->precision != CLB_F64) return bad("unsupported precision");
+    if (p->precision != CLB_F64 && p->precision != CLB_F16S && p->precision != CLB_F16N)
+        return bad("precision must be CLB_F64, CLB_F16S or CLB_F16N");
     if (!(p->Da > 0) || !(p->Pr > 0) || !(p->J > 0) || !(p->Gamma > 0) || !(p->sigma > 0))
         return bad("Da, Pr, J, Gamma and sigma must be positive");
     if (!(p->Ra >= 0)) return bad("Ra must be >= 0");
@@ -184,8 +202,10 @@ static void free_all(clb_handle* h) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
         cudaFree(h->f[i]);
         cudaFree(h->g[i]);
+        cudaFree(h->rec[i]);
     }
     cudaFree(h->coef);
+    cudaFree(h->phi32);
     cudaFree(h->ayg);
     cudaFree(h->scratch);
     cudaFree(h->snap);
@@ -196,26 +216,49 @@ static void free_all(clb_handle* h) {
 }
 
 // ------------------------------------------------------------------ kernels
-static void launch_step(clb_handle* h, cudaStream_t s) {
-    const int a = h->par, b = 1 - h->par;
+template <class P, typename K>
+static void step_as(clb_handle* h, cudaStream_t s, const AuxT<typename P::R>& A, const K& kp) {
+    using S = typename P::S;
+    const BufT<S> in = h->buf<S>(h->par), out = h->buf<S>(1 - h->par);
     const bool sh = h->prm.shift != 0, fo = h->prm.forchheimer != 0;
-    if (sh && fo)
-        k_step_f64<true, true><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
-    else if (sh)
-        k_step_f64<true, false><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
-    else if (fo)
-        k_step_f64<false, true><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
-    else
-        k_step_f64<false, false><<<h->grid, h->block, 0, s>>>(h->f[a], h->g[a], h->f[b], h->g[b], h->coef, h->ayg, h->kp);
-    h->par = b;
+    if (sh && fo) k_step<P, true, true><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
+    else if (sh) k_step<P, true, false><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
+    else if (fo) k_step<P, false, true><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
+    else k_step<P, false, false><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
+}
+
+static void launch_step(clb_handle* h, cudaStream_t s) {
+    if (h->prec == CLB_F16S) step_as<StoreH16>(h, s, h->aux32(), h->k32);
+    else if (h->prec == CLB_F16N) step_as<StoreH16N>(h, s, h->aux32(), h->k32);
+    else step_as<StoreF64>(h, s, h->aux64(), h->k64);
+    h->par = 1 - h->par;
+}
+
+template <class P, typename K>
+static void macros_as(clb_handle* h, const AuxT<typename P::R>& A, const K& kp, double* r, double* u, double* v,
+                      double* T) {
+    using S = typename P::S;
+    const BufT<S> in = h->buf<S>(h->par);
+    if (h->prm.forchheimer) k_macros<P, true><<<h->grid, h->block, 0, h->stream>>>(in, A, kp, r, u, v, T);
+    else k_macros<P, false><<<h->grid, h->block, 0, h->stream>>>(in, A, kp, r, u, v, T);
 }
 
 static void launch_macros(clb_handle* h, double* r, double* u, double* v, double* T) {
-    const int a = h->par;
-    if (h->prm.forchheimer)
-        k_macros_f64<true><<<h->grid, h->block, 0, h->stream>>>(h->f[a], h->g[a], h->coef, h->ayg, h->kp, r, u, v, T);
-    else
-        k_macros_f64<false><<<h->grid, h->block, 0, h->stream>>>(h->f[a], h->g[a], h->coef, h->ayg, h->kp, r, u, v, T);
+    if (h->prec == CLB_F16S) macros_as<StoreH16>(h, h->aux32(), h->k32, r, u, v, T);
+    else if (h->prec == CLB_F16N) macros_as<StoreH16N>(h, h->aux32(), h->k32, r, u, v, T);
+    else macros_as<StoreF64>(h, h->aux64(), h->k64, r, u, v, T);
+}
+
+template <class P, typename K>
+static void set_fields_as(clb_handle* h, const AuxT<typename P::R>& A, const K& kp, const double* d, long long n) {
+    using S = typename P::S;
+    k_set_fields<P><<<h->grid, h->block, 0, h->stream>>>(h->buf<S>(0), A, d, d + n, d + 2 * n, d + 3 * n, kp);
+}
+
+template <class P, typename K>
+static void nusselt_as(clb_handle* h, const AuxT<typename P::R>& A, const K& kp, int nb, int side, double scale) {
+    using S = typename P::S;
+    k_nusselt_partial<P><<<nb, kRedThreads, 0, h->stream>>>(h->buf<S>(h->par), A, kp, side, scale, h->partial);
 }
 
 // Capture kGraphSteps steps starting from buffer parity `par` into an
@@ -295,47 +338,87 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
     CKI(cudaGetDevice(&h->device));
     CKI(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
 
-    const int px = (p->nx + 31) / 32 * 32;
+    h->prec = p->precision;
+    const bool half = h->prec != CLB_F64;
+    h->es = half ? sizeof(__half) : sizeof(double);
+    const int px = (p->nx + 63) / 64 * 64;          // 128 B rows in FP16, 512 B in FP64
     h->lat.pitch = px;
-    KParams& K = h->kp;
-    K.g.nx = p->nx;
-    K.g.ny = p->ny;
-    K.g.px = px;
-    K.g.plane = (long long)px * p->ny;
-    K.g.wall_x = wall_x;
-    K.g.wall_y = wall_y;
-    for (int s = 0; s < 4; ++s) {
-        K.b.uw[s] = bc->u[s];
-        K.b.vw[s] = bc->v[s];
-        K.b.Tw[s] = bc->T[s];
-        K.b.iso[s] = bc->thermal[s] == CLB_ISOTHERMAL;
+    {
+        KParamsT<double> K{};
+        K.g.nx = p->nx;
+        K.g.ny = p->ny;
+        K.g.px = px;
+        K.g.plane = (long long)px * p->ny;
+        K.g.wall_x = wall_x;
+        K.g.wall_y = wall_y;
+        for (int s = 0; s < 4; ++s) {
+            K.b.uw[s] = bc->u[s];
+            K.b.vw[s] = bc->v[s];
+            K.b.Tw[s] = bc->T[s];
+            K.b.iso[s] = bc->thermal[s] == CLB_ISOTHERMAL;
+        }
+        K.p.ax = p->ax;
+        K.p.gbeta = lat.gbeta;
+        K.p.sigma = p->sigma;
+        K.p.inv_sigma = 1.0 / p->sigma;
+        K.p.cT2 = 0.5 * p->varpi;
+        K.p.sv = lat.sv;
+        K.p.sp = 0.5 * (lat.sb + lat.sv);
+        K.p.sm = 0.5 * (lat.sb - lat.sv);
+        K.p.s3 = p->s3;
+        K.p.s4 = p->s4;
+        K.p.om_a = 1.0 - lat.zeta_a;
+        K.p.c6 = (1.0 - 0.5 * p->s3) / 3.0;
+        K.p.ca = 1.0 - 0.5 * lat.sv;
+        K.p.cb8 = 1.0 - 0.5 * p->s4;
+        K.nuK = lat.nu / lat.K;
+        K.l1c = p->forchheimer ? 0.875 / std::sqrt(150.0 * lat.K) : 0.0;
+        K.T0 = p->T0;
+        h->k64 = K;
+        // FP16 form: same parameters in FP32, and the rest-state offsets the
+        // stored deviations are taken from: w_i rho_0 (rho_0 = 1) for f, the
+        // D2Q5 equilibrium at rest and T = T0 for g.
+        KParamsT<float>& k = h->k32;
+        k.g = K.g;
+        for (int s = 0; s < 4; ++s) {
+            k.b.uw[s] = (float)K.b.uw[s];
+            k.b.vw[s] = (float)K.b.vw[s];
+            k.b.Tw[s] = (float)K.b.Tw[s];
+            k.b.iso[s] = K.b.iso[s];
+        }
+        const double* pd = &K.p.ax;
+        float* pf = &k.p.ax;
+        for (size_t i = 0; i < sizeof(PhysT<double>) / sizeof(double); ++i) pf[i] = (float)pd[i];
+        k.nuK = (float)K.nuK;
+        k.l1c = (float)K.l1c;
+        k.T0 = (float)K.T0;
+        const double w9[9] = {16.0 / 36, 4.0 / 36, 4.0 / 36, 4.0 / 36, 4.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+        for (int i = 0; i < 9; ++i) k.wf[i] = (float)w9[i];
+        k.wg[0] = (float)((p->sigma - p->varpi) * p->T0);
+        for (int i = 1; i < 5; ++i) k.wg[i] = (float)(0.25 * p->varpi * p->T0);
     }
-    K.p.ax = p->ax;
-    K.p.gbeta = lat.gbeta;
-    K.p.inv_sigma = 1.0 / p->sigma;
-    K.p.cT2 = 0.5 * p->varpi;
-    K.p.sv = lat.sv;
-    K.p.sp = 0.5 * (lat.sb + lat.sv);
-    K.p.sm = 0.5 * (lat.sb - lat.sv);
-    K.p.s3 = p->s3;
-    K.p.s4 = p->s4;
-    K.p.om_a = 1.0 - lat.zeta_a;
-    K.p.c6 = (1.0 - 0.5 * p->s3) / 3.0;
-    K.p.ca = 1.0 - 0.5 * lat.sv;
-    K.p.cb8 = 1.0 - 0.5 * p->s4;
+    const Geo& G = h->k64.g;
     pick_launch(h);
 
-    const size_t fbytes = (size_t)K.g.plane * 9 * sizeof(double);
-    const size_t gbytes = (size_t)K.g.plane * 5 * sizeof(double);
+    const size_t fbytes = (size_t)G.plane * 9 * h->es;
+    const size_t gbytes = (size_t)G.plane * 5 * h->es;
     for (int i = 0; i < 2; ++i) {
         CKI(cudaMalloc(&h->f[i], fbytes));
         CKI(cudaMalloc(&h->g[i], gbytes));
         // the pitch padding is never read by the kernels; clear it once
         CKI(cudaMemsetAsync(h->f[i], 0, fbytes, h->stream));
         CKI(cudaMemsetAsync(h->g[i], 0, gbytes, h->stream));
+        if (h->prec == CLB_F16N) {
+            CKI(cudaMalloc(&h->rec[i], (size_t)G.plane * sizeof(uint2)));
+            CKI(cudaMemsetAsync(h->rec[i], 0, (size_t)G.plane * sizeof(uint2), h->stream));
+        }
     }
-    CKI(cudaMalloc(&h->coef, (size_t)n * sizeof(Coef)));
-    CKI(cudaMalloc(&h->ayg, (size_t)p->ny * sizeof(double)));
+    if (h->prec == CLB_F16S) CKI(cudaMalloc(&h->phi32, (size_t)n * sizeof(float)));
+    else if (h->prec == CLB_F16N) {
+        CKI(cudaMalloc(&h->phi32, (size_t)G.plane * sizeof(float)));
+        CKI(cudaMemsetAsync(h->phi32, 0, (size_t)G.plane * sizeof(float), h->stream));
+    } else CKI(cudaMalloc(&h->coef, (size_t)n * sizeof(CoefT<double>)));
+    CKI(cudaMalloc(&h->ayg, (size_t)p->ny * (half ? sizeof(float) : sizeof(double))));
     CKI(cudaMalloc(&h->scratch, (size_t)n * 4 * sizeof(double)));
     CKI(cudaMalloc(&h->snap, (size_t)n * 3 * sizeof(double)));
     h->n_partial = reduce_partials(p->nx, p->ny);
@@ -343,15 +426,24 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
     CKI(cudaMalloc(&h->result, 8 * sizeof(double)));
     CKI(cudaMallocHost(&h->host_res, 8 * sizeof(double)));
 
-    // per-node constants from phi (staged through the scratch buffer)
+    // per-node constants (FP64 form) or FP32 porosity (FP16 form), staged
+    // through the scratch buffer
     CKI(cudaMemcpyAsync(h->scratch, phi, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    k_coef<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, h->coef, n, lat.nu, lat.K,
-                                                                 p->forchheimer);
+    if (half)
+        k_phi32<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, h->phi32, p->nx, p->ny, px,
+                                                                      h->prec == CLB_F16N);
+    else
+        k_coef<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, h->coef, n, lat.nu, lat.K,
+                                                                     p->forchheimer);
     CKI(cudaGetLastError());
     // a_y per row with g beta T0 folded in: G_y = g beta T + (a_y - g beta T0)
     std::vector<double> ay(p->ny);
     for (int y = 0; y < p->ny; ++y) ay[y] = (ay_row ? ay_row[y] : p->ay) - lat.gbeta * p->T0;
-    CKI(cudaMemcpyAsync(h->ayg, ay.data(), ay.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    std::vector<float> ayf(ay.begin(), ay.end());
+    if (half)
+        CKI(cudaMemcpyAsync(h->ayg, ayf.data(), ayf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    else
+        CKI(cudaMemcpyAsync(h->ayg, ay.data(), ay.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CKI(cudaStreamSynchronize(h->stream));
 
     // start at rest: rho = 1, u = 0, T = T_init, filled on the device
@@ -390,8 +482,9 @@ static int set_fields_from_scratch(clb_handle* h) {
     const long long n = (long long)h->prm.nx * h->prm.ny;
     double* d = h->scratch;
     h->par = 0;
-    k_set_fields_f64<<<h->grid, h->block, 0, h->stream>>>(h->f[0], h->g[0], h->coef, d, d + n, d + 2 * n,
-                                                         d + 3 * n, h->prm.sigma, h->kp);
+    if (h->prec == CLB_F16S) set_fields_as<StoreH16>(h, h->aux32(), h->k32, d, n);
+    else if (h->prec == CLB_F16N) set_fields_as<StoreH16N>(h, h->aux32(), h->k32, d, n);
+    else set_fields_as<StoreF64>(h, h->aux64(), h->k64, d, n);
     CK(h, cudaGetLastError());
     h->t = 0;
     // residual reference = the new state
@@ -461,9 +554,10 @@ extern "C" int clb_nusselt(clb_handle* h, int32_t side, double* nu) {
     if (len < 2 || depth < 3) return fail(h, CLB_ERR_ARG, "clb_nusselt: grid too small");
     const int nb = (len + kRedThreads - 1) / kRedThreads;
     if (nb > h->n_partial) return fail(h, CLB_ERR_ARG, "clb_nusselt: too many partials");
-    const int a = h->par;
     const double scale = -h->lat.L / h->prm.dT / (double)(len - 1);
-    k_nusselt_partial<<<nb, kRedThreads, 0, h->stream>>>(h->g[a], h->coef, h->kp, side, scale, h->partial);
+    if (h->prec == CLB_F16S) nusselt_as<StoreH16>(h, h->aux32(), h->k32, nb, side, scale);
+    else if (h->prec == CLB_F16N) nusselt_as<StoreH16N>(h, h->aux32(), h->k32, nb, side, scale);
+    else nusselt_as<StoreF64>(h, h->aux64(), h->k64, nb, side, scale);
     k_sum_partials<<<1, kRedThreads, 0, h->stream>>>(h->partial, nb, 1, h->result);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(h->host_res, h->result, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -506,29 +600,42 @@ extern "C" int clb_lattice_params(const clb_handle* h, clb_lattice* out) {
 
 // Checkpoint layout: 8 int64 header words (magic, version, nx, ny,
 // precision, t, 0, 0), then f (9 planes) and g (5 planes), each plane ny*nx
-// doubles without pitch padding.
+// stored values (FP64, or the FP16 deviations) without pitch padding.
 static const int64_t kMagic = 0x434c42314750554cLL;
 
 extern "C" size_t clb_state_bytes(const clb_handle* h) {
     if (!h) return 0;
-    return 8 * sizeof(int64_t) + (size_t)14 * h->prm.nx * h->prm.ny * sizeof(double);
+    return 8 * sizeof(int64_t) + (size_t)h->prm.nx * h->prm.ny * h->node_bytes();
+}
+
+// Copy the 14 distribution planes (and the record plane of the FP16N form)
+// between a packed host image and the pitched device buffer `b`.
+static int copy_state(clb_handle* h, int b, char* host, bool to_host) {
+    const Geo& G = h->geo();
+    const int planes = h->prec == CLB_F16N ? 15 : 14;
+    size_t off = 0;
+    for (int i = 0; i < planes; ++i) {
+        const size_t es = i < 14 ? h->es : sizeof(uint2);
+        const size_t row = (size_t)h->prm.nx * es, pitch = (size_t)G.px * es;
+        char* dev = i < 9 ? (char*)h->f[b] + (size_t)i * G.plane * es
+                   : i < 14 ? (char*)h->g[b] + (size_t)(i - 9) * G.plane * es
+                            : (char*)h->rec[b];
+        if (to_host)
+            CK(h, cudaMemcpy2DAsync(host + off, row, dev, pitch, row, h->prm.ny, cudaMemcpyDeviceToHost, h->stream));
+        else
+            CK(h, cudaMemcpy2DAsync(dev, pitch, host + off, row, row, h->prm.ny, cudaMemcpyHostToDevice, h->stream));
+        off += row * h->prm.ny;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return CLB_OK;
 }
 
 extern "C" int clb_get_state(clb_handle* h, void* buf, size_t bytes) {
     if (!h || !buf) return CLB_ERR_ARG;
     if (bytes < clb_state_bytes(h)) return fail(h, CLB_ERR_ARG, "clb_get_state: buffer too small");
-    int64_t* hd = (int64_t*)buf;
     int64_t hdr[8] = {kMagic, 1, h->prm.nx, h->prm.ny, h->prm.precision, h->t, 0, 0};
-    std::memcpy(hd, hdr, sizeof hdr);
-    char* p = (char*)buf + sizeof hdr;
-    const size_t row = (size_t)h->prm.nx * sizeof(double), pitch = (size_t)h->kp.g.px * sizeof(double);
-    const size_t plane = row * h->prm.ny;
-    for (int i = 0; i < 14; ++i) {
-        const double* src = i < 9 ? h->f[h->par] + i * h->kp.g.plane : h->g[h->par] + (i - 9) * h->kp.g.plane;
-        CK(h, cudaMemcpy2DAsync(p + i * plane, row, src, pitch, row, h->prm.ny, cudaMemcpyDeviceToHost, h->stream));
-    }
-    CK(h, cudaStreamSynchronize(h->stream));
-    return CLB_OK;
+    std::memcpy(buf, hdr, sizeof hdr);
+    return copy_state(h, h->par, (char*)buf + sizeof hdr, true);
 }
 
 extern "C" int clb_set_state(clb_handle* h, const void* buf, size_t bytes) {
@@ -539,16 +646,10 @@ extern "C" int clb_set_state(clb_handle* h, const void* buf, size_t bytes) {
     if (hdr[0] != kMagic || hdr[1] != 1 || hdr[2] != h->prm.nx || hdr[3] != h->prm.ny ||
         hdr[4] != h->prm.precision)
         return fail(h, CLB_ERR_STATE, "clb_set_state: checkpoint does not match this simulation");
-    const char* p = (const char*)buf + sizeof hdr;
-    const size_t row = (size_t)h->prm.nx * sizeof(double), pitch = (size_t)h->kp.g.px * sizeof(double);
-    const size_t plane = row * h->prm.ny;
     h->par = 0;
-    for (int i = 0; i < 14; ++i) {
-        double* dst = i < 9 ? h->f[0] + i * h->kp.g.plane : h->g[0] + (i - 9) * h->kp.g.plane;
-        CK(h, cudaMemcpy2DAsync(dst, pitch, p + i * plane, row, row, h->prm.ny, cudaMemcpyHostToDevice, h->stream));
-    }
+    const int rc = copy_state(h, 0, (char*)buf + sizeof hdr, false);
+    if (rc != CLB_OK) return rc;
     h->t = hdr[5];
-    CK(h, cudaStreamSynchronize(h->stream));
     return CLB_OK;
 }
 

@@ -1,0 +1,721 @@
+// clb_kernels.cuh -- device code of the coupled porous cascaded LB step.
+//
+// One thread owns one node.  The fused kernel pulls the 9 + 5 post-collision
+// values of the previous step from the node's neighbours (streaming, Eqs. 18
+// and 35, as a pull), forms the macroscopic state (Eqs. 20, 22-23, 36, 4),
+// collides both lattices (Eqs. 11 and 28) and writes the post-collision
+// values back to the node's own slot of the other buffer (ping-pong).  Wall
+// nodes rebuild their pre-collision values by non-equilibrium extrapolation
+// from the inward neighbour, whose values they pull themselves, so a step is
+// one launch with no inter-thread dependency.
+//
+// The collision is evaluated in "delta" form: with m~ the central moments
+// of Eq. 12 and Delta = m~* - m~ from Eq. 11, linearity gives
+//   f* = M^-1 N^-1 (m~ + Delta) = f + M^-1 N^-1 Delta,
+// so only N m (rows 3..8, Eq. 14), the relaxation increments, N^-1 Delta
+// (Eq. A1, with Delta_0 = 0) and M^-1 are needed; every product of the
+// dense matrices is expanded by hand into the few multiply-adds its
+// non-zero pattern requires.  With s_0 = s_1 = 1 the first-order central
+// moments after collision are rho F / 2 (Eq. 11, Eq. 17), and with
+// zeta_T = zeta_e = zeta_nu = 1 the thermal moments n~0, n~3, n~4 relax
+// straight to Eq. 32, so they are never formed.
+//
+// Two storage forms share this arithmetic (templated on the real type R):
+//   StoreF64 : FP64 distributions, FP64 arithmetic, per-node FP64 constants
+//              (1/phi, phi/2, phi nu/K, l1 or 1/(2 l0)) precomputed at init.
+//              On GB300 FP64 issues at 2 DFMA/clk/SM, so this form is bound
+//              by FP64 instruction throughput, not by HBM; precomputing the
+//              constants removes their divisions and square roots.
+//   StoreH16 : FP16 storage of each distribution's deviation from its
+//              rest-state value (w_i rho_0 for f, the equilibrium at T0 for
+//              g), FP32 arithmetic, constants recomputed per node from an
+//              FP32 porosity (FP32 is plentiful; bytes are not).  60 B per
+//              node update: bound by HBM.  The deviation of the rest
+//              population g_0 is O(Delta T), so FP16 quantises T at ~2e-4 of
+//              Delta T every step -- too coarse for converged Nusselt numbers.
+//   StoreH16N: FP16 storage of each post-collision value's deviation from
+//              the local equilibrium f^eq(rho, u; phi), g^eq(T, u) of the
+//              node that wrote it, plus that node's (rho - 1, u, T - T0) as
+//              four halves.  Writer and reader rebuild the baseline from the
+//              same stored halves, so the baseline needs no precision; only
+//              the small non-equilibrium remainder is quantised.  FP32
+//              arithmetic, 1/phi in FP32; 76 B per node update.
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#ifndef CLB_HD
+#define CLB_HD __host__ __device__ __forceinline__
+#endif
+
+namespace clb {
+
+// Per-node constants derived from the porosity (Eqs. 4, 5, 23).
+template <typename R>
+struct alignas(4 * sizeof(R)) CoefT {
+    R ip;    // 1 / phi
+    R hphi;  // phi / 2
+    R dar;   // phi nu / K (Darcy coefficient of Eq. 4)
+    R aux;   // Forchheimer: l1 = phi F_phi / (2 sqrt K); else 1 / (2 l0)
+};
+
+struct Geo {
+    int nx, ny, px;       // grid and row pitch (elements)
+    long long plane;      // px * ny
+    int wall_x, wall_y;   // W/E resp. S/N are walls
+};
+
+template <typename R>
+struct BndT {
+    R uw[4], vw[4], Tw[4];
+    int iso[4];
+};
+
+template <typename R>
+struct PhysT {
+    R ax, gbeta, sigma, inv_sigma, cT2;   // a_x, g*beta, sigma, 1/sigma, c_sT^2
+    R sv, s3, s4, om_a;                   // relaxation rates, om_a = 1 - zeta_alpha
+    R sp, sm;                             // (s_b + s_v)/2, (s_b - s_v)/2: (k20, k02) block of Eq. 15
+    R c6;                                 // (1 - s3/2) / 3  (Eq. 11 rows 6, 7 with Eq. 17)
+    R ca, cb8;                            // unit-shift variant: 1 - s_v/2, 1 - s4/2
+};
+
+template <typename R>
+struct KParamsT {
+    Geo g;
+    BndT<R> b;
+    PhysT<R> p;
+    R nuK;        // nu / K       (FP16 forms: per-node constants from phi)
+    R l1c;        // 0.875 / sqrt(150 K): l1 = l1c / sqrt(phi)
+    R T0;         // reference temperature (baseline record of the FP16N form)
+    R wf[9];      // rest-state offsets of the stored distributions (FP16 form)
+    R wg[5];
+};
+
+// Pointers that are not distributions: per-node constants (FP64 form),
+// porosity (FP16 rest-shifted form, dense) or 1/phi (FP16 equilibrium-shifted
+// form, pitched like the planes), and a_y - g beta T0 per row.
+template <typename R>
+struct AuxT {
+    const CoefT<R>* coef;
+    const float* phi;
+    const float* ip;
+    const R* ayg;
+};
+
+// One ping-pong buffer: distribution planes, and for the equilibrium-shifted
+// FP16 form the per-node baseline record (rho - 1, u_x, u_y, T - T0) as four
+// halves.
+template <typename S>
+struct BufT {
+    S* f;
+    S* g;
+    uint2* rec;
+};
+
+template <typename S>
+__host__ __device__ inline BufT<const S> as_const(const BufT<S>& b) {
+    return BufT<const S>{b.f, b.g, b.rec};
+}
+
+__device__ __forceinline__ int wrap_lo(int a, int n) { return a < 0 ? a + n : a; }
+__device__ __forceinline__ int wrap_hi(int a, int n) { return a >= n ? a - n : a; }
+
+// Plane offsets of the values streaming into (x, y): f_i(x) = f*_i(x - e_i)
+// (Eqs. 18 and 35), with periodic wrap (walled directions never wrap for
+// the nodes that pull).
+__device__ __forceinline__ void sources(const Geo& G, int x, int y, long long (&o)[9]) {
+    const int xm = wrap_lo(x - 1, G.nx), xp = wrap_hi(x + 1, G.nx);
+    const int ym = wrap_lo(y - 1, G.ny), yp = wrap_hi(y + 1, G.ny);
+    const long long r0 = (long long)y * G.px, rm = (long long)ym * G.px, rp = (long long)yp * G.px;
+    o[0] = r0 + x;
+    o[1] = r0 + xm;
+    o[2] = rm + x;
+    o[3] = r0 + xp;
+    o[4] = rp + x;
+    o[5] = rm + xm;
+    o[6] = rm + xp;
+    o[7] = rp + xp;
+    o[8] = rp + xm;
+}
+
+// Raw moments of Eq. 12, M f, with the shared partial sums of M's rows.
+template <typename R>
+struct Mom9T {
+    R rho, jx, jy, k20, k02, k11, k21, k12, k22;
+};
+
+template <typename R>
+CLB_HD Mom9T<R> moments9(const R (&f)[9]) {
+    const R a = f[5] + f[7], b = f[6] + f[8];
+    const R c = f[5] - f[7], d = f[6] - f[8];
+    const R s13 = f[1] + f[3], s24 = f[2] + f[4];
+    Mom9T<R> k;
+    k.k22 = a + b;
+    k.k11 = a - b;
+    k.k21 = c + d;
+    k.k12 = c - d;
+    k.k20 = s13 + k.k22;
+    k.k02 = s24 + k.k22;
+    k.jx = (f[1] - f[3]) + k.k12;
+    k.jy = (f[2] - f[4]) + k.k21;
+    k.rho = (f[0] + s13) + (s24 + k.k22);
+    return k;
+}
+
+// Macroscopic velocity by Eqs. 22-23 and force by Eq. 4 at a node with
+// density rho, momentum j = sum e f and temperature T.
+template <typename R, bool FORCH>
+CLB_HD void macro_velocity(R rho, R jx, R jy, R T, R ayg, const CoefT<R>& c, const PhysT<R>& P, R& X, R& Y, R& Fx,
+                           R& Fy) {
+    const R irho = R(1) / rho;
+    const R Gy = fma(P.gbeta, T, ayg);           // a_y + g beta (T - T0), T0 folded into ayg
+    const R hGx = c.hphi * P.ax, hGy = c.hphi * Gy;
+    const R vx = fma(jx, irho, hGx), vy = fma(jy, irho, hGy);
+    R cF;
+    if (FORCH) {
+        const R l0 = fma(R(0.25), c.dar, R(0.5));
+        const R vm = sqrt(fma(vx, vx, vy * vy));
+        const R den = l0 + sqrt(fma(c.aux, vm, l0 * l0));
+        const R inv = R(1) / den;
+        X = vx * inv;
+        Y = vy * inv;
+        cF = fma(R(2) * c.aux, vm * inv, c.dar);   // phi nu/K + phi F_phi/sqrt(K) |u|
+    } else {
+        X = vx * c.aux;
+        Y = vy * c.aux;
+        cF = c.dar;
+    }
+    Fx = fma(-cF, X, hGx + hGx);
+    Fy = fma(-cF, Y, hGy + hGy);
+}
+
+// Porous flow equilibrium f^eq = M^-1 m^eq (Eq. 19).
+template <typename R>
+CLB_HD void feq9(R rho, R X, R Y, R ip, R (&fe)[9]) {
+    const R X2 = X * X, Y2 = Y * Y;
+    const R r3 = rho * R(1.0 / 3.0);
+    const R m1 = rho * X, m2 = rho * Y;
+    const R m3 = fma(m1 * ip, X, r3);
+    const R m4 = fma(m2 * ip, Y, r3);
+    const R m5 = m1 * Y * ip;
+    const R m6 = fma(m1 * ip, X * Y, r3 * Y);
+    const R m7 = fma(m2 * ip, X * Y, r3 * X);
+    const R m8 = rho * R(1.0 / 9.0) + r3 * ip * (X2 + Y2) + rho * X2 * Y2 * ip * ip;
+    fe[0] = rho - m3 - m4 + m8;
+    fe[1] = R(0.5) * (m1 + m3 - m7 - m8);
+    fe[2] = R(0.5) * (m2 + m4 - m6 - m8);
+    fe[3] = R(0.5) * (-m1 + m3 + m7 - m8);
+    fe[4] = R(0.5) * (-m2 + m4 + m6 - m8);
+    fe[5] = R(0.25) * (m5 + m6 + m7 + m8);
+    fe[6] = R(0.25) * (-m5 + m6 - m7 + m8);
+    fe[7] = R(0.25) * (m5 - m6 - m7 + m8);
+    fe[8] = R(0.25) * (-m5 - m6 + m7 + m8);
+}
+
+// Thermal equilibrium g^eq = M_T^-1 n^eq (Eq. 33; equals Eq. 34).
+template <typename R>
+CLB_HD void geq5(R T, R X, R Y, R sigma, R cT2, R (&ge)[5]) {
+    const R n1 = X * T, n2 = Y * T;
+    const R n3 = fma(X, n1, cT2 * T), n4 = fma(Y, n2, cT2 * T);
+    ge[0] = sigma * T - n3 - n4;
+    ge[1] = R(0.5) * (n1 + n3);
+    ge[2] = R(0.5) * (n2 + n4);
+    ge[3] = R(0.5) * (n3 - n1);
+    ge[4] = R(0.5) * (n4 - n2);
+}
+
+// Flow collision (Eq. 11) in delta form; see the file comment.
+template <typename R, bool SHIFT>
+CLB_HD void collide9(R (&f)[9], const Mom9T<R>& k, R rho, R X, R Y, R Fx, R Fy, R ip, const PhysT<R>& P) {
+    const R rFx = rho * Fx, rFy = rho * Fy;
+    const R px = fma(rho, X, -k.jx), py = fma(rho, Y, -k.jy);   // -(k~10), -(k~01)
+    const R X2 = X * X, Y2 = Y * Y, XY = X * Y;
+    const R X2p = X + X, Y2p = Y + Y, XY4 = R(4) * XY;
+    const R r3 = rho * R(1.0 / 3.0), r9 = rho * R(1.0 / 9.0);
+    const R D1 = fma(R(0.5), rFx, px);
+    const R D2 = fma(R(0.5), rFy, py);
+    R r3v, r4v, r5v, r6v, r7v, r8v;
+    if (SHIFT) {
+        // central moments m~3..m~8 = rows 3..8 of N (Eq. 14) times m
+        const R ipX = ip * X, ipY = ip * Y;
+        const R t = px - k.jx, tp = py - k.jy;        // rho X - 2 jx, rho Y - 2 jy
+        const R Xjy = X * k.jy, Yjx = Y * k.jx;
+        const R c3 = fma(ipX, t, k.k20);
+        const R c4 = fma(ipY, tp, k.k02);
+        const R c5 = fma(ip, fma(Y, px, -Xjy), k.k11);
+        const R w = fma(-Y, t, Xjy);
+        const R c6 = fma(ipX, w, fma(-Y, k.k20, fma(-X2p, k.k11, k.k21)));
+        const R wp = fma(-X, tp, Yjx);
+        const R c7 = fma(ipY, wp, fma(-X, k.k02, fma(-Y2p, k.k11, k.k12)));
+        R A = Y2 * k.k20;
+        A = fma(X2, k.k02, A);
+        A = fma(XY4, k.k11, A);
+        A = fma(-Y2p, k.k21, A);
+        A = fma(-X2p, k.k12, A);
+        A = fma(-(ip * XY), w + Xjy, A);
+        const R c8 = fma(ip, A, k.k22);
+        // increments of Eq. 11 (Lambda of Eq. 15 with s_0 = s_1 = 1)
+        const R e3 = r3 - c3, e4 = r3 - c4;
+        const R D3 = fma(P.sp, e3, P.sm * e4);
+        const R D4 = fma(P.sp, e4, P.sm * e3);
+        const R D5 = -P.sv * c5;
+        const R D6 = fma(-P.s3, c6, P.c6 * rFy);
+        const R D7 = fma(-P.s3, c7, P.c6 * rFx);
+        const R D8 = P.s4 * (r9 - c8);
+        // back to raw moments: N^-1 Delta (Eq. A1), Delta_0 = 0
+        const R ipX2 = ipX + ipX, ipY2 = ipY + ipY;
+        r3v = fma(ipX2, D1, D3);
+        r4v = fma(ipY2, D2, D4);
+        r5v = fma(ipY, D1, fma(ipX, D2, D5));
+        r6v = fma(ipX, fma(Y2p, D1, X * D2), fma(Y, D3, fma(X2p, D5, D6)));
+        r7v = fma(ipY, fma(Y, D1, X2p * D2), fma(X, D4, fma(Y2p, D5, D7)));
+        R B = Y2 * D3;
+        B = fma(X2, D4, B);
+        B = fma(XY4, D5, B);
+        B = fma(Y2p, D6, B);
+        B = fma(X2p, D7, B);
+        B = fma(R(2) * ip * XY, fma(Y, D1, X * D2), B);
+        r8v = fma(ip, B, D8);
+    } else {
+        // unit shift: relax raw moments towards Eq. 19's m^eq with Eq. 19's S
+        const R ipr = ip * rho;
+        const R meq3 = fma(ipr * X, X, r3), meq4 = fma(ipr * Y, Y, r3);
+        const R meq5 = ipr * XY;
+        const R meq6 = fma(ipr * X2, Y, r3 * Y), meq7 = fma(ipr * Y2, X, r3 * X);
+        const R meq8 = r9 + r3 * ip * (X2 + Y2) + ipr * ip * X2 * Y2;
+        const R S3 = R(2) * ip * X * rFx, S4 = R(2) * ip * Y * rFy;
+        const R S5 = ip * fma(X, rFy, Y * rFx);
+        const R S6 = fma(ip, fma(X2, rFy, R(2) * XY * rFx), rFy * R(1.0 / 3.0));
+        const R S7 = fma(ip, fma(Y2, rFx, R(2) * XY * rFy), rFx * R(1.0 / 3.0));
+        const R S8 = R(2.0 / 3.0) * ip * fma(X, rFx, Y * rFy) + R(2) * ip * ip * XY * fma(Y, rFx, X * rFy);
+        // (k20, k02) block: -Lambda_b (m - m^eq) + (I - Lambda_b / 2) S
+        const R d3 = k.k20 - meq3, d4 = k.k02 - meq4;
+        r3v = -fma(P.sp, d3, P.sm * d4) + S3 - R(0.5) * fma(P.sp, S3, P.sm * S4);
+        r4v = -fma(P.sm, d3, P.sp * d4) + S4 - R(0.5) * fma(P.sm, S3, P.sp * S4);
+        r5v = fma(-P.sv, k.k11 - meq5, P.ca * S5);
+        r6v = fma(-P.s3, k.k21 - meq6, R(3) * P.c6 * S6);
+        r7v = fma(-P.s3, k.k12 - meq7, R(3) * P.c6 * S7);
+        r8v = fma(-P.s4, k.k22 - meq8, P.cb8 * S8);
+    }
+    // f* = f + M^-1 r, r = (0, D1, D2, r3..r8)
+    const R pa = r3v - r8v, qa = D1 - r7v;
+    const R pb = r4v - r8v, qb = D2 - r6v;
+    const R u1 = r8v + r5v, u2 = r8v - r5v, v1 = r6v + r7v, v2 = r6v - r7v;
+    f[0] += (r8v - r3v) - r4v;
+    f[1] = fma(R(0.5), pa + qa, f[1]);
+    f[3] = fma(R(0.5), pa - qa, f[3]);
+    f[2] = fma(R(0.5), pb + qb, f[2]);
+    f[4] = fma(R(0.5), pb - qb, f[4]);
+    f[5] = fma(R(0.25), u1 + v1, f[5]);
+    f[7] = fma(R(0.25), u1 - v1, f[7]);
+    f[6] = fma(R(0.25), u2 + v2, f[6]);
+    f[8] = fma(R(0.25), u2 - v2, f[8]);
+}
+
+// Temperature collision (Eq. 28) with zeta_T = zeta_e = zeta_nu = 1:
+// g* = M_T^-1 N_T^-1 n~*, n~* = (sigma T, (1 - zeta_a) n~1, (1 - zeta_a) n~2,
+// c_sT^2 T, c_sT^2 T), where n~1 = n1 - u_x T (Eq. 31 with sigma T = n0).
+// Back-shifting (N_T^-1) gives n1* = u_x T + n~1*, n3* = u_x^2 T + 2 u_x n~1*
+// + c_sT^2 T.  The unit-shift variant relaxes the raw moments towards
+// Eq. 33 instead: n1* as above, n3* = (c_sT^2 + u_x^2) T.
+template <typename R, bool SHIFT>
+CLB_HD void collide5(R (&g)[5], R n0, R T, R X, R Y, const PhysT<R>& P) {
+    const R XT = X * T, YT = Y * T;
+    const R c1 = P.om_a * ((g[1] - g[3]) - XT);   // (1 - zeta_a) n~1
+    const R c2 = P.om_a * ((g[2] - g[4]) - YT);
+    const R n1 = XT + c1, n2 = YT + c2;
+    const R cT = P.cT2 * T;
+    const R n3 = SHIFT ? fma(X + X, c1, fma(X, XT, cT)) : fma(X, XT, cT);
+    const R n4 = SHIFT ? fma(Y + Y, c2, fma(Y, YT, cT)) : fma(Y, YT, cT);
+    g[0] = (n0 - n3) - n4;
+    g[1] = R(0.5) * (n1 + n3);
+    g[2] = R(0.5) * (n2 + n4);
+    g[3] = R(0.5) * (n3 - n1);
+    g[4] = R(0.5) * (n4 - n2);
+}
+
+// Force of Eq. 4 at a node whose velocity is imposed (wall nodes).
+template <typename R, bool FORCH>
+CLB_HD void force_at(R X, R Y, R T, R ayg, const CoefT<R>& c, const PhysT<R>& P, R& Fx, R& Fy) {
+    const R Gy = fma(P.gbeta, T, ayg);
+    R cF = c.dar;
+    if (FORCH) cF = fma(R(2) * c.aux, sqrt(fma(X, X, Y * Y)), c.dar);
+    Fx = fma(-cF, X, R(2) * c.hphi * P.ax);
+    Fy = fma(-cF, Y, R(2) * c.hphi * Gy);
+}
+
+
+template <typename R>
+__device__ __forceinline__ R sum5(const R (&v)[5]) {
+    return ((v[0] + v[1]) + (v[2] + v[3])) + v[4];
+}
+
+// ---------------------------------------------------------------- storage
+// A storage policy reads the streamed values of a node (pull9 / pull5),
+// writes a node's post-collision values (store) and gives the per-node
+// constants (coef).
+struct StoreF64 {
+    using R = double;
+    using S = double;
+    static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
+                                                 int y, R (&f)[9]) {
+        long long o[9];
+        sources(K.g, x, y, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = __ldg(B.f + i * K.g.plane + o[i]);
+    }
+    static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
+                                                 int y, R (&g)[5]) {
+        long long o[9];
+        sources(K.g, x, y, o);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = __ldg(B.g + i * K.g.plane + o[i]);
+    }
+    static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
+                                                 const R (&f)[9], const R (&g)[5], R, R, R, R, R) {
+        const long long o = (long long)y * K.g.px + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) B.f[i * K.g.plane + o] = f[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) B.g[i * K.g.plane + o] = g[i];
+    }
+    template <bool FORCH>
+    static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
+        return A.coef[(long long)y * K.g.nx + x];
+    }
+};
+
+// FP32 constants of a node from its porosity (Eqs. 4, 5, 23).
+template <bool FORCH>
+__device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, const KParamsT<float>& K) {
+    CoefT<float> c;
+    c.ip = ip;
+    c.hphi = 0.5f * p;
+    c.dar = p * K.nuK;
+    // Ergun (Eq. 5): l1 = phi F_phi / (2 sqrt K) = 0.875 / sqrt(150 K phi)
+    c.aux = FORCH ? K.l1c * rsqrtf(p) : 1.0f / (1.0f + 0.5f * c.dar);
+    return c;
+}
+
+struct StoreH16 {
+    using R = float;
+    using S = __half;
+    static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
+                                                 int y, R (&f)[9]) {
+        long long o[9];
+        sources(K.g, x, y, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = K.wf[i] + __half2float(__ldg(B.f + i * K.g.plane + o[i]));
+    }
+    static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
+                                                 int y, R (&g)[5]) {
+        long long o[9];
+        sources(K.g, x, y, o);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) g[i] = K.wg[i] + __half2float(__ldg(B.g + i * K.g.plane + o[i]));
+    }
+    static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
+                                                 const R (&f)[9], const R (&g)[5], R, R, R, R, R) {
+        const long long o = (long long)y * K.g.px + x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) B.f[i * K.g.plane + o] = __float2half_rn(f[i] - K.wf[i]);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) B.g[i * K.g.plane + o] = __float2half_rn(g[i] - K.wg[i]);
+    }
+    template <bool FORCH>
+    static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
+        const float p = __ldg(A.phi + (long long)y * K.g.nx + x);
+        return coef_from_phi<FORCH>(p, 1.0f / p, K);
+    }
+};
+
+// Baseline (rho, u, T, 1/phi) of the node whose record sits at plane offset o.
+struct Base {
+    float rho, X, Y, T, ip;
+};
+
+__device__ __forceinline__ Base load_base(const BufT<const __half>& B, const AuxT<float>& A,
+                                          const KParamsT<float>& K, long long o) {
+    const uint2 r = __ldg(B.rec + o);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
+    Base s;
+    s.rho = 1.0f + a.x;
+    s.X = a.y;
+    s.Y = b.x;
+    s.T = K.T0 + b.y;
+    s.ip = __ldg(A.ip + o);
+    return s;
+}
+
+struct StoreH16N {
+    using R = float;
+    using S = __half;
+    static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
+                                                 int y, R (&f)[9]) {
+        long long o[9];
+        sources(K.g, x, y, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const Base s = load_base(B, A, K, o[i]);
+            R fe[9];
+            feq9(s.rho, s.X, s.Y, s.ip, fe);
+            f[i] = fe[i] + __half2float(__ldg(B.f + i * K.g.plane + o[i]));
+        }
+    }
+    static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
+                                                 int y, R (&g)[5]) {
+        long long o[9];
+        sources(K.g, x, y, o);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const Base s = load_base(B, A, K, o[i]);
+            R ge[5];
+            geq5(s.T, s.X, s.Y, K.p.sigma, K.p.cT2, ge);
+            g[i] = ge[i] + __half2float(__ldg(B.g + i * K.g.plane + o[i]));
+        }
+    }
+    // The record is rounded first and the baseline rebuilt from the rounded
+    // halves, exactly as a reader will rebuild it.
+    static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
+                                                 const R (&f)[9], const R (&g)[5], R rho, R X, R Y, R T, R ip) {
+        const long long o = (long long)y * K.g.px + x;
+        const __half2 a = __floats2half2_rn(rho - 1.0f, X);
+        const __half2 b = __floats2half2_rn(Y, T - K.T0);
+        uint2 r;
+        r.x = *reinterpret_cast<const unsigned int*>(&a);
+        r.y = *reinterpret_cast<const unsigned int*>(&b);
+        B.rec[o] = r;
+        const float2 fa = __half22float2(a), fb = __half22float2(b);
+        R fe[9], ge[5];
+        feq9(1.0f + fa.x, fa.y, fb.x, ip, fe);
+        geq5(K.T0 + fb.y, fa.y, fb.x, K.p.sigma, K.p.cT2, ge);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) B.f[i * K.g.plane + o] = __float2half_rn(f[i] - fe[i]);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) B.g[i * K.g.plane + o] = __float2half_rn(g[i] - ge[i]);
+    }
+    template <bool FORCH>
+    static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
+        const float ip = __ldg(A.ip + (long long)y * K.g.px + x);
+        return coef_from_phi<FORCH>(1.0f / ip, ip, K);
+    }
+};
+
+// Inward normal of a wall node and the sides that set its velocity and
+// temperature.  Returns false for an interior node.
+struct WallInfo {
+    int dx, dy, su, st;
+};
+
+template <typename R>
+__device__ __forceinline__ bool wall_info(const Geo& G, const BndT<R>& B, int x, int y, WallInfo& w) {
+    int vs = -1, hs = -1;
+    w.dx = 0;
+    w.dy = 0;
+    if (G.wall_x) {
+        if (x == 0) { w.dx = 1; vs = 0; }
+        else if (x == G.nx - 1) { w.dx = -1; vs = 1; }
+    }
+    if (G.wall_y) {
+        if (y == 0) { w.dy = 1; hs = 2; }
+        else if (y == G.ny - 1) { w.dy = -1; hs = 3; }
+    }
+    if (vs < 0 && hs < 0) return false;
+    w.su = vs >= 0 ? vs : hs;
+    w.st = (vs >= 0 && B.iso[vs]) ? vs : ((hs >= 0 && B.iso[hs]) ? hs : -1);
+    return true;
+}
+
+// Pre-collision state of a wall node by non-equilibrium extrapolation from
+// its inward neighbour s = (x + dx, y + dy), pulled here from the same
+// post-collision buffer as every other node:
+//   f(b) = f^eq(rho_s, u_w; phi_b) + f(s) - f^eq(rho_s, u_s; phi_s)
+//   g(b) = g^eq(T_b, u_w) + g(s) - g^eq(T_s, u_s)
+// T_b = T_w (isothermal) or (4 T_s - T_ss) / 3 (adiabatic).
+template <class P, bool FORCH>
+__device__ __forceinline__ void wall_state(const BufT<const typename P::S>& Bin, const AuxT<typename P::R>& A,
+                                           const KParamsT<typename P::R>& K, int x, int y, const WallInfo& w,
+                                           const CoefT<typename P::R>& cb, typename P::R (&f)[9],
+                                           typename P::R (&g)[5], typename P::R& rho, typename P::R& X,
+                                           typename P::R& Y, typename P::R& T, typename P::R& n0) {
+    using R = typename P::R;
+    const int sx = x + w.dx, sy = y + w.dy;
+    R fs[9], gs[5];
+    P::pull9(Bin, A, K, sx, sy, fs);
+    P::pull5(Bin, A, K, sx, sy, gs);
+    const Mom9T<R> ks = moments9(fs);
+    const R Ts = sum5(gs) * K.p.inv_sigma;
+    const CoefT<R> cs = P::template coef<FORCH>(A, K, sx, sy);
+    R Xs, Ys, Fxs, Fys;
+    macro_velocity<R, FORCH>(ks.rho, ks.jx, ks.jy, Ts, A.ayg[sy], cs, K.p, Xs, Ys, Fxs, Fys);
+    R Tb;
+    if (w.st >= 0) {
+        Tb = K.b.Tw[w.st];
+    } else {
+        R gss[5];
+        P::pull5(Bin, A, K, x + 2 * w.dx, y + 2 * w.dy, gss);
+        const R Tss = sum5(gss) * K.p.inv_sigma;
+        Tb = (R(4) * Ts - Tss) * R(1.0 / 3.0);
+    }
+    const R uw = K.b.uw[w.su], vw = K.b.vw[w.su];
+    R fb[9], fe[9];
+    feq9(ks.rho, uw, vw, cb.ip, fb);
+    feq9(ks.rho, Xs, Ys, cs.ip, fe);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = fb[i] + (fs[i] - fe[i]);
+    R gb[5], ge[5];
+    geq5(Tb, uw, vw, K.p.sigma, K.p.cT2, gb);
+    geq5(Ts, Xs, Ys, K.p.sigma, K.p.cT2, ge);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) g[i] = gb[i] + (gs[i] - ge[i]);
+    rho = ks.rho;
+    X = uw;
+    Y = vw;
+    T = Tb;
+    n0 = sum5(g);
+}
+
+// Macroscopic state of any node at the current time level (pre-collision
+// values in f, g; wall nodes rebuilt by non-equilibrium extrapolation).
+template <class P, bool FORCH>
+__device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin, const AuxT<typename P::R>& A,
+                                           const KParamsT<typename P::R>& K, int x, int y,
+                                           const CoefT<typename P::R>& c, typename P::R (&f)[9],
+                                           typename P::R (&g)[5], Mom9T<typename P::R>& k, typename P::R& rho,
+                                           typename P::R& X, typename P::R& Y, typename P::R& T,
+                                           typename P::R& Fx, typename P::R& Fy, typename P::R& n0) {
+    using R = typename P::R;
+    WallInfo w;
+    if (!wall_info(K.g, K.b, x, y, w)) {
+        P::pull9(Bin, A, K, x, y, f);
+        P::pull5(Bin, A, K, x, y, g);
+        k = moments9(f);
+        n0 = sum5(g);
+        T = n0 * K.p.inv_sigma;
+        rho = k.rho;
+        macro_velocity<R, FORCH>(rho, k.jx, k.jy, T, A.ayg[y], c, K.p, X, Y, Fx, Fy);
+    } else {
+        wall_state<P, FORCH>(Bin, A, K, x, y, w, c, f, g, rho, X, Y, T, n0);
+        k = moments9(f);
+        force_at<R, FORCH>(X, Y, T, A.ayg[y], c, K.p, Fx, Fy);
+    }
+}
+
+// ---------------------------------------------------------------- kernels
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(256) k_step(const BufT<typename P::S> in, const BufT<typename P::S> out,
+                                              const AuxT<typename P::R> A, const KParamsT<typename P::R> K) {
+    using R = typename P::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= K.g.nx || y >= K.g.ny) return;
+    const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
+    R f[9], g[5];
+    R rho, X, Y, T, Fx, Fy, n0;
+    Mom9T<R> k;
+    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Fx, Fy, n0);
+    collide9<R, SHIFT>(f, k, rho, X, Y, Fx, Fy, c.ip, K.p);
+    collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
+    P::store(out, K, x, y, f, g, rho, X, Y, T, c.ip);
+}
+
+// Macroscopic fields at the current time level (dense ny*nx FP64 outputs).
+template <class P, bool FORCH>
+__global__ void k_macros(const BufT<typename P::S> in, const AuxT<typename P::R> A,
+                         const KParamsT<typename P::R> K, double* __restrict__ orho, double* __restrict__ oux,
+                         double* __restrict__ ouy, double* __restrict__ oT) {
+    using R = typename P::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= K.g.nx || y >= K.g.ny) return;
+    const long long n = (long long)y * K.g.nx + x;
+    const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
+    R f[9], g[5], rho, X, Y, T, Fx, Fy, n0;
+    Mom9T<R> k;
+    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Fx, Fy, n0);
+    if (orho) orho[n] = (double)rho;
+    if (oux) oux[n] = (double)X;
+    if (ouy) ouy[n] = (double)Y;
+    if (oT) oT[n] = (double)T;
+}
+
+// Post-collision buffers whose pull reproduces the local equilibria of the
+// given fields: slot i of node y holds f_i^eq of the node y + e_i that
+// pulls it (periodic wrap; on a walled side the slot is never pulled and
+// takes the node's own value).  The node's own fields are its baseline
+// record in the FP16N form.
+template <class P>
+__global__ void k_set_fields(const BufT<typename P::S> out, const AuxT<typename P::R> A,
+                             const double* __restrict__ rho, const double* __restrict__ ux,
+                             const double* __restrict__ uy, const double* __restrict__ T,
+                             const KParamsT<typename P::R> K) {
+    using R = typename P::R;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= K.g.nx || y >= K.g.ny) return;
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    R f[9], g[5];
+#pragma unroll 1
+    for (int i = 0; i < 9; ++i) {
+        int zx = x + ex[i], zy = y + ey[i];
+        if (zx < 0 || zx >= K.g.nx) zx = K.g.wall_x ? x : wrap_hi(wrap_lo(zx, K.g.nx), K.g.nx);
+        if (zy < 0 || zy >= K.g.ny) zy = K.g.wall_y ? y : wrap_hi(wrap_lo(zy, K.g.ny), K.g.ny);
+        const long long z = (long long)zy * K.g.nx + zx;
+        const R zr = (R)rho[z], zu = (R)ux[z], zv = (R)uy[z], zT = (R)T[z];
+        R fe[9];
+        feq9(zr, zu, zv, P::template coef<false>(A, K, zx, zy).ip, fe);
+        f[i] = fe[i];
+        if (i < 5) {
+            R ge[5];
+            geq5(zT, zu, zv, K.p.sigma, K.p.cT2, ge);
+            g[i] = ge[i];
+        }
+    }
+    const long long n = (long long)y * K.g.nx + x;
+    P::store(out, K, x, y, f, g, (R)rho[n], (R)ux[n], (R)uy[n], (R)T[n], P::template coef<false>(A, K, x, y).ip);
+}
+
+// Four consecutive dense fields of n values set to constants.
+__global__ void k_fill4(double* __restrict__ d, long long n, double a, double b, double c, double e) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    d[i] = a;
+    d[n + i] = b;
+    d[2 * n + i] = c;
+    d[3 * n + i] = e;
+}
+
+// Per-node FP64 constants from the porosity (Eqs. 4, 5, 23).
+__global__ void k_coef(const double* __restrict__ phi, CoefT<double>* __restrict__ coef, long long n, double nu,
+                       double K, int forch) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double p = phi[i];
+    CoefT<double> c;
+    c.ip = 1.0 / p;
+    c.hphi = 0.5 * p;
+    c.dar = p * nu / K;
+    if (forch) {
+        const double Fphi = 1.75 / sqrt(150.0 * p * p * p);      // Ergun, Eq. 5
+        c.aux = 0.5 * p * Fphi / sqrt(K);                         // l1 of Eq. 23
+    } else {
+        c.aux = 1.0 / (1.0 + 0.5 * c.dar);                        // 1 / (2 l0), Eq. 23
+    }
+    coef[i] = c;
+}
+
+// FP32 porosity (dense) for the FP16 rest-shifted form, or FP32 1/phi
+// (pitched, px per row) for the FP16 equilibrium-shifted form.
+__global__ void k_phi32(const double* __restrict__ phi, float* __restrict__ out, int nx, int ny, int px, int inv) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)nx * ny) return;
+    const long long y = i / nx, x = i - y * nx;
+    if (inv) out[y * px + x] = (float)(1.0 / phi[i]);
+    else out[i] = (float)phi[i];
+}
+
+}  // namespace clb

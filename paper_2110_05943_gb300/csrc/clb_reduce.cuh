@@ -3,7 +3,7 @@
 // warp shuffles -> per-block partials -> one block), so results are
 // bit-reproducible run to run.
 #pragma once
-#include "clb_f64.cuh"
+#include "clb_kernels.cuh"
 
 namespace clb {
 
@@ -40,28 +40,33 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 
 // Temperature (Eq. 36) of node (x, y) at the current time level; wall nodes
 // give their wall value or the second-order adiabatic extrapolation.
-__device__ __forceinline__ double temperature_at(const double* __restrict__ g, const KParams& K, int x, int y) {
+template <class P>
+__device__ __forceinline__ double temperature_at(const BufT<const typename P::S>& B, const AuxT<typename P::R>& A,
+                                                 const KParamsT<typename P::R>& K, int x, int y) {
+    using R = typename P::R;
     WallInfo w;
-    double v[5];
+    R v[5];
     if (!wall_info(K.g, K.b, x, y, w)) {
-        pull5(g, K.g, x, y, v);
-        return (((v[0] + v[1]) + (v[2] + v[3])) + v[4]) * K.p.inv_sigma;
+        P::pull5(B, A, K, x, y, v);
+        return (double)(sum5(v) * K.p.inv_sigma);
     }
-    if (w.st >= 0) return K.b.Tw[w.st];
-    pull5(g, K.g, x + w.dx, y + w.dy, v);
-    const double Ts = (((v[0] + v[1]) + (v[2] + v[3])) + v[4]) * K.p.inv_sigma;
-    pull5(g, K.g, x + 2 * w.dx, y + 2 * w.dy, v);
-    const double Tss = (((v[0] + v[1]) + (v[2] + v[3])) + v[4]) * K.p.inv_sigma;
-    return (4.0 * Ts - Tss) * (1.0 / 3.0);
+    if (w.st >= 0) return (double)K.b.Tw[w.st];
+    P::pull5(B, A, K, x + w.dx, y + w.dy, v);
+    const R Ts = sum5(v) * K.p.inv_sigma;
+    P::pull5(B, A, K, x + 2 * w.dx, y + 2 * w.dy, v);
+    const R Tss = sum5(v) * K.p.inv_sigma;
+    return (double)((R(4) * Ts - Tss) * R(1.0 / 3.0));
 }
 
 // Per-block partial sums of the trapezoid-weighted local Nusselt number
-// Nu = -L dT/dn / dT along one wall; `scale` = -L / (dT (len - 1)).
-__global__ void __launch_bounds__(kRedThreads) k_nusselt_partial(const double* __restrict__ g,
-                                                                 const Coef* __restrict__ coef,
-                                                                 const KParams K, int side, double scale,
-                                                                 double* __restrict__ partial) {
+// Nu = -L dT/dn / dT along one wall (FP64); `scale` = -L / (dT (len - 1)).
+template <class P>
+__global__ void __launch_bounds__(kRedThreads) k_nusselt_partial(const BufT<typename P::S> in,
+                                                                 const AuxT<typename P::R> A,
+                                                                 const KParamsT<typename P::R> K, int side,
+                                                                 double scale, double* __restrict__ partial) {
     __shared__ double sh[kRedThreads / 32];
+    const BufT<const typename P::S> B = as_const(in);
     const bool along_y = side == 0 || side == 1;
     const int len = along_y ? K.g.ny : K.g.nx;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -69,18 +74,26 @@ __global__ void __launch_bounds__(kRedThreads) k_nusselt_partial(const double* _
     if (i < len) {
         double T0, T1, T2, d;
         if (side == 0) {
-            T0 = temperature_at(g, K, 0, i); T1 = temperature_at(g, K, 1, i); T2 = temperature_at(g, K, 2, i);
+            T0 = temperature_at<P>(B, A, K, 0, i);
+            T1 = temperature_at<P>(B, A, K, 1, i);
+            T2 = temperature_at<P>(B, A, K, 2, i);
             d = (-3.0 * T0 + 4.0 * T1 - T2) * 0.5;
         } else if (side == 1) {
             const int e = K.g.nx - 1;
-            T0 = temperature_at(g, K, e, i); T1 = temperature_at(g, K, e - 1, i); T2 = temperature_at(g, K, e - 2, i);
+            T0 = temperature_at<P>(B, A, K, e, i);
+            T1 = temperature_at<P>(B, A, K, e - 1, i);
+            T2 = temperature_at<P>(B, A, K, e - 2, i);
             d = (3.0 * T0 - 4.0 * T1 + T2) * 0.5;
         } else if (side == 2) {
-            T0 = temperature_at(g, K, i, 0); T1 = temperature_at(g, K, i, 1); T2 = temperature_at(g, K, i, 2);
+            T0 = temperature_at<P>(B, A, K, i, 0);
+            T1 = temperature_at<P>(B, A, K, i, 1);
+            T2 = temperature_at<P>(B, A, K, i, 2);
             d = (-3.0 * T0 + 4.0 * T1 - T2) * 0.5;
         } else {
             const int e = K.g.ny - 1;
-            T0 = temperature_at(g, K, i, e); T1 = temperature_at(g, K, i, e - 1); T2 = temperature_at(g, K, i, e - 2);
+            T0 = temperature_at<P>(B, A, K, i, e);
+            T1 = temperature_at<P>(B, A, K, i, e - 1);
+            T2 = temperature_at<P>(B, A, K, i, e - 2);
             d = (3.0 * T0 - 4.0 * T1 + T2) * 0.5;
         }
         const double wgt = (i == 0 || i == len - 1) ? 0.5 : 1.0;
@@ -88,7 +101,6 @@ __global__ void __launch_bounds__(kRedThreads) k_nusselt_partial(const double* _
     }
     v = block_sum(v, sh);
     if (threadIdx.x == 0) partial[blockIdx.x] = v;
-    (void)coef;
 }
 
 // Residual sums over all nodes: |u - u_ref|^2, |u|^2, (T - T_ref)^2, T^2;

@@ -1,0 +1,120 @@
+"""The reduced-precision forms against the FP64 oracle and the FP64 GPU path.
+
+CLB_F16S stores each distribution in FP16 as its deviation from the rest
+state; CLB_F16N as its deviation from the local equilibrium of the node
+that wrote it (that node's rho, u, T stored in FP16 as the baseline).  Both
+compute in FP32.  Bounds are measured errors times ~4 (recorded beside each
+check); the target for a converged run is the FP64 mean Nusselt number
+within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+from cases import CAVITY, PERIODIC, build, field_errors
+
+pytestmark = pytest.mark.gpu
+F16S, F16N = 1, 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def steady(sim, chunk=2000, tol=1e-8, max_steps=3_000_000):
+    sim.residual()
+    while sim.time < max_steps:
+        sim.step(chunk)
+        ru, rT = sim.residual()
+        if max(ru, rT) < tol:
+            break
+    return sim.time
+
+
+def test_f16n_cavity_64_10k_steps_vs_oracle():
+    """64^2 cavity, 10,000 steps.  Measured: rho-1 1.4e-3, u 5.1e-4, T 2.3e-5,
+    Nu 3.7e-6 relative (the rest-shifted form: 0.46, 0.24, 0.18, 0.79)."""
+    orc, sim = build(64, 64, 0.6, Ra=1e4, Da=1e-2, Pr=1.0, precision=F16N)
+    orc.step(10_000)
+    sim.step(10_000)
+    e = field_errors(sim.macros(), orc.macros())
+    assert e["rho-1"] < 6e-3 and e["ux"] < 2e-3 and e["uy"] < 2e-3 and e["T"] < 1e-4, e
+    assert abs(sim.nusselt(0) / orc.nusselt(0) - 1) < 2e-5
+
+
+def test_f16n_random_porosity_ragged_vs_oracle():
+    """300 x 37 seeded-porosity cavity, 1,500 steps.  Measured: rho-1 4.4e-3,
+    u 1.0e-3, T 1.7e-4."""
+    from paper_2110_05943_gb300.inputs import porosity_field
+    phi = porosity_field(300, 37, seed=11, ell=8.0)
+    orc, sim = build(300, 37, phi, Ra=1e6, Da=1e-3, Pr=0.71, sigma=0.8, precision=F16N)
+    orc.step(1500)
+    sim.step(1500)
+    e = field_errors(sim.macros(), orc.macros())
+    assert e["rho-1"] < 2e-2 and e["ux"] < 4e-3 and e["uy"] < 4e-3 and e["T"] < 7e-4, e
+
+
+def test_f16n_steady_nusselt_within_1e4_of_fp64():
+    """Table 1 row Da 1e-2, Ra 1e4, phi 0.6 on 128^2: steady mean Nusselt
+    number of the FP16N form within 1e-4 of the FP64 path (measured 9.3e-6)."""
+    _, s64 = build(128, 128, 0.6, Ra=1e4, Da=1e-2, Pr=1.0, with_oracle=False)
+    _, s16 = build(128, 128, 0.6, Ra=1e4, Da=1e-2, Pr=1.0, precision=F16N, with_oracle=False)
+    steady(s64, tol=1e-10)
+    steady(s16, tol=1e-6, max_steps=1_000_000)
+    assert abs(s16.nusselt(0) / s64.nusselt(0) - 1) < 1e-4
+
+
+@pytest.mark.parametrize("shift,forch", [(False, True), (True, False)])
+def test_f16n_variants_track_oracle(shift, forch):
+    from paper_2110_05943_gb300.inputs import porosity_field
+    phi = porosity_field(40, 40, seed=2, ell=6.0)
+    orc, sim = build(40, 40, phi, Ra=1e5, Da=1e-2, Pr=0.71, shift=shift, forchheimer=forch, precision=F16N)
+    orc.step(2000)
+    sim.step(2000)
+    e = field_errors(sim.macros(), orc.macros())
+    assert e["ux"] < 5e-3 and e["uy"] < 5e-3 and e["T"] < 5e-4, e
+
+
+def test_f16s_tracks_oracle_over_short_times():
+    """The rest-shifted form is within FP16 resolution of the oracle for a
+    short transient (measured after 200 steps on a 64^2 cavity)."""
+    orc, sim = build(64, 64, 0.6, Ra=1e4, Da=1e-2, Pr=1.0, precision=F16S)
+    orc.step(200)
+    sim.step(200)
+    e = field_errors(sim.macros(), orc.macros())
+    assert e["T"] < 5e-3 and e["ux"] < 5e-2, e
+
+
+@pytest.mark.parametrize("prec", [F16S, F16N])
+def test_f16_periodic_set_fields_and_checkpoint(prec):
+    """Periodic domain from smooth random fields: the initial macros
+    reproduce the given fields to FP16 resolution, and a checkpoint
+    resumes bit for bit."""
+    from paper_2110_05943_gb300.inputs import smooth_fields
+    nx, ny = 50, 40
+    rho, ux, uy, T = smooth_fields(nx, ny, seed=9)
+    _, sim = build(nx, ny, 0.7, Ra=1e5, Da=1e-2, Pr=0.71, sigma=1.3, L=32, kind=PERIODIC, T=(None,) * 4,
+                   precision=prec, with_oracle=False)
+    sim.set_fields(rho, ux, uy, T)
+    r0, u0, v0, T0 = sim.macros()
+    assert np.abs(T0 - T).max() < 2e-3 and np.abs(u0 - ux).max() < 2e-4
+    sim.step(123)
+    st = sim.get_state()
+    sim.step(50)
+    a = sim.macros()
+    sim.set_state(st)
+    sim.step(50)
+    b = sim.macros()
+    for x, y in zip(a, b):
+        assert np.array_equal(x, y)
+
+
+def test_f16n_small_grids_and_corners():
+    for nx, ny in ((4, 4), (5, 33), (33, 5)):
+        orc, sim = build(nx, ny, 0.7, Ra=1e4, Da=1e-2, precision=F16N)
+        orc.step(300)
+        sim.step(300)
+        e = field_errors(sim.macros(), orc.macros())
+        assert e["T"] < 1e-3 and np.isfinite(list(e.values())).all(), (nx, ny, e)
