@@ -63,7 +63,8 @@ struct clb_handle {
     int64_t t = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
-    dim3 block, grid;
+    dim3 block, grid;          // one node per thread
+    dim3 block2, grid2;        // two nodes per thread (FP16 forms)
     std::string err;
 
     AuxT<double> aux64() const { return AuxT<double>{coef, nullptr, nullptr, (const double*)ayg}; }
@@ -195,6 +196,13 @@ static void pick_launch(clb_handle* h) {
     if (by > ny) by = ny < 1 ? 1 : ny;
     h->block = dim3(bx, by);
     h->grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by);
+    const int npair = (nx + 1) / 2;
+    int bx2 = 64;
+    while (bx2 > 32 && bx2 / 2 >= npair) bx2 /= 2;
+    int by2 = 128 / bx2;
+    if (by2 > ny) by2 = ny < 1 ? 1 : ny;
+    h->block2 = dim3(bx2, by2);
+    h->grid2 = dim3((npair + bx2 - 1) / bx2, (ny + by2 - 1) / by2);
 }
 
 static void free_all(clb_handle* h) {
@@ -227,9 +235,22 @@ static void step_as(clb_handle* h, cudaStream_t s, const AuxT<typename P::R>& A,
     else k_step<P, false, false><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
 }
 
+// FP16 forms: two nodes per thread (k_step2), grid over node pairs.
+template <class P>
+static void step2_as(clb_handle* h, cudaStream_t s) {
+    using S = typename P::S;
+    const BufT<S> in = h->buf<S>(h->par), out = h->buf<S>(1 - h->par);
+    const AuxT<float> A = h->aux32();
+    const bool sh = h->prm.shift != 0, fo = h->prm.forchheimer != 0;
+    if (sh && fo) k_step2<P, true, true><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
+    else if (sh) k_step2<P, true, false><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
+    else if (fo) k_step2<P, false, true><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
+    else k_step2<P, false, false><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
+}
+
 static void launch_step(clb_handle* h, cudaStream_t s) {
-    if (h->prec == CLB_F16S) step_as<StoreH16>(h, s, h->aux32(), h->k32);
-    else if (h->prec == CLB_F16N) step_as<StoreH16N>(h, s, h->aux32(), h->k32);
+    if (h->prec == CLB_F16S) step2_as<StoreH16>(h, s);
+    else if (h->prec == CLB_F16N) step2_as<StoreH16N>(h, s);
     else step_as<StoreF64>(h, s, h->aux64(), h->k64);
     h->par = 1 - h->par;
 }
@@ -398,6 +419,10 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
         for (int i = 1; i < 5; ++i) k.wg[i] = (float)(0.25 * p->varpi * p->T0);
     }
     const Geo& G = h->k64.g;
+    if (half && (long long)G.plane * 9 > 2147483647LL) {
+        fail(h, CLB_ERR_ARG, "clb_init: grid too large for the FP16 forms' 32-bit offsets (9 * ny * pitch >= 2^31)");
+        return bail(CLB_ERR_ARG);
+    }
     pick_launch(h);
 
     const size_t fbytes = (size_t)G.plane * 9 * h->es;

@@ -46,10 +46,12 @@
 #include <stdint.h>
 
 #ifndef CLB_HD
-#define CLB_HD __host__ __device__ __forceinline__
+#define CLB_HD __device__ __forceinline__
 #endif
 
 namespace clb {
+
+using ::fma;   // keep the float / double overloads visible next to fma(f2, f2, f2)
 
 // Per-node constants derived from the porosity (Eqs. 4, 5, 23).
 template <typename R>
@@ -124,11 +126,13 @@ __device__ __forceinline__ int wrap_hi(int a, int n) { return a >= n ? a - n : a
 
 // Plane offsets of the values streaming into (x, y): f_i(x) = f*_i(x - e_i)
 // (Eqs. 18 and 35), with periodic wrap (walled directions never wrap for
-// the nodes that pull).
-__device__ __forceinline__ void sources(const Geo& G, int x, int y, long long (&o)[9]) {
+// the nodes that pull).  I = long long for FP64 buffers, int for FP16 ones
+// (clb_init checks that every FP16 offset fits).
+template <typename I>
+__device__ __forceinline__ void sources(const Geo& G, int x, int y, I (&o)[9]) {
     const int xm = wrap_lo(x - 1, G.nx), xp = wrap_hi(x + 1, G.nx);
     const int ym = wrap_lo(y - 1, G.ny), yp = wrap_hi(y + 1, G.ny);
-    const long long r0 = (long long)y * G.px, rm = (long long)ym * G.px, rp = (long long)yp * G.px;
+    const I r0 = (I)y * G.px, rm = (I)ym * G.px, rp = (I)yp * G.px;
     o[0] = r0 + x;
     o[1] = r0 + xm;
     o[2] = rm + x;
@@ -139,6 +143,70 @@ __device__ __forceinline__ void sources(const Geo& G, int x, int y, long long (&
     o[7] = rp + xp;
     o[8] = rp + xm;
 }
+
+// ---------------------------------------------------------------- packed FP32
+// Two FP32 lanes in one 64-bit register, operated on by the f32x2 forms of
+// add / sub / mul / fma (sm_100 and later): the FP16 forms run two nodes per
+// thread through the same templated arithmetic with R = f2, halving the
+// FP32 instructions issued per node.
+struct f2 {
+    unsigned long long v;
+    f2() = default;
+    __device__ __forceinline__ explicit f2(double c) { v = pack((float)c, (float)c); }
+    static __device__ __forceinline__ unsigned long long pack(float a, float b) {
+        unsigned long long r;
+        asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+        return r;
+    }
+    static __device__ __forceinline__ f2 make(float a, float b) {
+        f2 r;
+        r.v = pack(a, b);
+        return r;
+    }
+    __device__ __forceinline__ float lo() const { return __uint_as_float((unsigned)(v & 0xffffffffull)); }
+    __device__ __forceinline__ float hi() const { return __uint_as_float((unsigned)(v >> 32)); }
+};
+
+__device__ __forceinline__ f2 operator+(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 operator*(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ f2 operator-(f2 a) {
+    f2 r;
+    r.v = a.v ^ 0x8000000080000000ull;   // flip both sign bits
+    return r;
+}
+__device__ __forceinline__ f2& operator+=(f2& a, f2 b) { return a = a + b; }
+__device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// Reciprocal and square root: IEEE in FP64 (the parity path); in FP32 the
+// hardware approximations (relative error ~1e-7, far below the FP16 storage
+// resolution of the forms that compute in FP32).
+CLB_HD double recip(double x) { return 1.0 / x; }
+CLB_HD double sqroot(double x) { return sqrt(x); }
+__device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ float sqroot(float x) {
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ f2 recip(f2 x) { return f2::make(recip(x.lo()), recip(x.hi())); }
+__device__ __forceinline__ f2 sqroot(f2 x) { return f2::make(sqroot(x.lo()), sqroot(x.hi())); }
 
 // Raw moments of Eq. 12, M f, with the shared partial sums of M's rows.
 template <typename R>
@@ -169,16 +237,16 @@ CLB_HD Mom9T<R> moments9(const R (&f)[9]) {
 template <typename R, bool FORCH>
 CLB_HD void macro_velocity(R rho, R jx, R jy, R T, R ayg, const CoefT<R>& c, const PhysT<R>& P, R& X, R& Y, R& Fx,
                            R& Fy) {
-    const R irho = R(1) / rho;
+    const R irho = recip(rho);
     const R Gy = fma(P.gbeta, T, ayg);           // a_y + g beta (T - T0), T0 folded into ayg
     const R hGx = c.hphi * P.ax, hGy = c.hphi * Gy;
     const R vx = fma(jx, irho, hGx), vy = fma(jy, irho, hGy);
     R cF;
     if (FORCH) {
         const R l0 = fma(R(0.25), c.dar, R(0.5));
-        const R vm = sqrt(fma(vx, vx, vy * vy));
-        const R den = l0 + sqrt(fma(c.aux, vm, l0 * l0));
-        const R inv = R(1) / den;
+        const R vm = sqroot(fma(vx, vx, vy * vy));
+        const R den = l0 + sqroot(fma(c.aux, vm, l0 * l0));
+        const R inv = recip(den);
         X = vx * inv;
         Y = vy * inv;
         cF = fma(R(2) * c.aux, vm * inv, c.dar);   // phi nu/K + phi F_phi/sqrt(K) |u|
@@ -341,7 +409,7 @@ template <typename R, bool FORCH>
 CLB_HD void force_at(R X, R Y, R T, R ayg, const CoefT<R>& c, const PhysT<R>& P, R& Fx, R& Fy) {
     const R Gy = fma(P.gbeta, T, ayg);
     R cF = c.dar;
-    if (FORCH) cF = fma(R(2) * c.aux, sqrt(fma(X, X, Y * Y)), c.dar);
+    if (FORCH) cF = fma(R(2) * c.aux, sqroot(fma(X, X, Y * Y)), c.dar);
     Fx = fma(-cF, X, R(2) * c.hphi * P.ax);
     Fy = fma(-cF, Y, R(2) * c.hphi * Gy);
 }
@@ -351,6 +419,39 @@ template <typename R>
 __device__ __forceinline__ R sum5(const R (&v)[5]) {
     return ((v[0] + v[1]) + (v[2] + v[3])) + v[4];
 }
+
+// Packing of per-node constants and model parameters for the paired path.
+__device__ __forceinline__ CoefT<f2> pack_coef(const CoefT<float>& a, const CoefT<float>& b) {
+    CoefT<f2> c;
+    c.ip = f2::make(a.ip, b.ip);
+    c.hphi = f2::make(a.hphi, b.hphi);
+    c.dar = f2::make(a.dar, b.dar);
+    c.aux = f2::make(a.aux, b.aux);
+    return c;
+}
+
+__device__ __forceinline__ PhysT<f2> splat(const PhysT<float>& p) {
+    PhysT<f2> q;
+    q.ax = f2(p.ax);
+    q.gbeta = f2(p.gbeta);
+    q.sigma = f2(p.sigma);
+    q.inv_sigma = f2(p.inv_sigma);
+    q.cT2 = f2(p.cT2);
+    q.sv = f2(p.sv);
+    q.s3 = f2(p.s3);
+    q.s4 = f2(p.s4);
+    q.om_a = f2(p.om_a);
+    q.sp = f2(p.sp);
+    q.sm = f2(p.sm);
+    q.c6 = f2(p.c6);
+    q.ca = f2(p.ca);
+    q.cb8 = f2(p.cb8);
+    return q;
+}
+
+// Directions whose source lies in the same column (e_x = 0): for two nodes
+// (x0, x0 + 1) with x0 even their sources are adjacent and 4-byte aligned.
+__device__ __forceinline__ constexpr bool column_dir(int i) { return i == 0 || i == 2 || i == 4; }
 
 // ---------------------------------------------------------------- storage
 // A storage policy reads the streamed values of a node (pull9 / pull5),
@@ -362,16 +463,21 @@ struct StoreF64 {
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
                                                  int y, R (&f)[9]) {
         long long o[9];
-        sources(K.g, x, y, o);
+        sources<long long>(K.g, x, y, o);
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = __ldg(B.f + i * K.g.plane + o[i]);
     }
     static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
                                                  int y, R (&g)[5]) {
         long long o[9];
-        sources(K.g, x, y, o);
+        sources<long long>(K.g, x, y, o);
 #pragma unroll
         for (int i = 0; i < 5; ++i) g[i] = __ldg(B.g + i * K.g.plane + o[i]);
+    }
+    static __device__ __forceinline__ void pull(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
+                                                int y, R (&f)[9], R (&g)[5]) {
+        pull9(B, A, K, x, y, f);
+        pull5(B, A, K, x, y, g);
     }
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
                                                  const R (&f)[9], const R (&g)[5], R, R, R, R, R) {
@@ -395,7 +501,7 @@ __device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, const K
     c.hphi = 0.5f * p;
     c.dar = p * K.nuK;
     // Ergun (Eq. 5): l1 = phi F_phi / (2 sqrt K) = 0.875 / sqrt(150 K phi)
-    c.aux = FORCH ? K.l1c * rsqrtf(p) : 1.0f / (1.0f + 0.5f * c.dar);
+    c.aux = FORCH ? K.l1c * rsqrtf(p) : recip(1.0f + 0.5f * c.dar);
     return c;
 }
 
@@ -404,30 +510,73 @@ struct StoreH16 {
     using S = __half;
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
                                                  int y, R (&f)[9]) {
-        long long o[9];
-        sources(K.g, x, y, o);
+        int o[9];
+        sources<int>(K.g, x, y, o);
+        const int Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = K.wf[i] + __half2float(__ldg(B.f + i * K.g.plane + o[i]));
+        for (int i = 0; i < 9; ++i) f[i] = K.wf[i] + __half2float(__ldg(B.f + i * Q + o[i]));
     }
     static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
                                                  int y, R (&g)[5]) {
-        long long o[9];
-        sources(K.g, x, y, o);
+        int o[9];
+        sources<int>(K.g, x, y, o);
+        const int Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = K.wg[i] + __half2float(__ldg(B.g + i * K.g.plane + o[i]));
+        for (int i = 0; i < 5; ++i) g[i] = K.wg[i] + __half2float(__ldg(B.g + i * Q + o[i]));
+    }
+    static __device__ __forceinline__ void pull(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
+                                                int y, R (&f)[9], R (&g)[5]) {
+        pull9(B, A, K, x, y, f);
+        pull5(B, A, K, x, y, g);
     }
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
                                                  const R (&f)[9], const R (&g)[5], R, R, R, R, R) {
-        const long long o = (long long)y * K.g.px + x;
+        const int o = y * K.g.px + x, Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * K.g.plane + o] = __float2half_rn(f[i] - K.wf[i]);
+        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = __float2half_rn(f[i] - K.wf[i]);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * K.g.plane + o] = __float2half_rn(g[i] - K.wg[i]);
+        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = __float2half_rn(g[i] - K.wg[i]);
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
-        const float p = __ldg(A.phi + (long long)y * K.g.nx + x);
-        return coef_from_phi<FORCH>(p, 1.0f / p, K);
+        const float p = __ldg(A.phi + y * K.g.nx + x);
+        return coef_from_phi<FORCH>(p, recip(p), K);
+    }
+    // Two interior nodes (x0, x0 + 1), x0 even.
+    static __device__ __forceinline__ void pull2(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x0,
+                                                 int y, f2 (&f)[9], f2 (&g)[5]) {
+        int o0[9], o1[9];
+        sources<int>(K.g, x0, y, o0);
+        sources<int>(K.g, x0 + 1, y, o1);
+        const int Q = (int)K.g.plane;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            float2 v;
+            if (column_dir(i)) v = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.f + i * Q + o0[i])));
+            else v = make_float2(__half2float(__ldg(B.f + i * Q + o0[i])), __half2float(__ldg(B.f + i * Q + o1[i])));
+            f[i] = f2(K.wf[i]) + f2::make(v.x, v.y);
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            float2 v;
+            if (column_dir(i)) v = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.g + i * Q + o0[i])));
+            else v = make_float2(__half2float(__ldg(B.g + i * Q + o0[i])), __half2float(__ldg(B.g + i * Q + o1[i])));
+            g[i] = f2(K.wg[i]) + f2::make(v.x, v.y);
+        }
+    }
+    static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
+                                                  const f2 (&f)[9], const f2 (&g)[5], f2, f2, f2, f2, f2) {
+        const int o = y * K.g.px + x0, Q = (int)K.g.plane;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const f2 d = f[i] - f2(K.wf[i]);
+            *reinterpret_cast<__half2*>(B.f + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const f2 d = g[i] - f2(K.wg[i]);
+            *reinterpret_cast<__half2*>(B.g + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+        }
     }
 };
 
@@ -437,7 +586,7 @@ struct Base {
 };
 
 __device__ __forceinline__ Base load_base(const BufT<const __half>& B, const AuxT<float>& A,
-                                          const KParamsT<float>& K, long long o) {
+                                          const KParamsT<float>& K, int o) {
     const uint2 r = __ldg(B.rec + o);
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
@@ -450,57 +599,193 @@ __device__ __forceinline__ Base load_base(const BufT<const __half>& B, const Aux
     return s;
 }
 
+// One component of the porous equilibrium f^eq = M^-1 m^eq (Eq. 19), written
+// out per direction (the value a puller needs from each source):
+//   f0 = rho (4/9) - (2/3) A (X^2 + Y^2) + A ip X^2 Y^2,                 A = rho / phi
+//   f1,3 = (1/2)[ (2/9) rho +- (2/3) rho X + A ((2/3) X^2 - Y^2 / 3 -+ X Y^2) - A ip X^2 Y^2 ]
+//   f2,4 = the same with X <-> Y
+//   f5..8 = (1/4)[ rho / 9 + (rho / 3)(sx X + sy Y) + A ((X^2 + Y^2) / 3 + sx sy X Y + sy X^2 Y + sx X Y^2)
+//                  + A ip X^2 Y^2 ],  (sx, sy) = e_i
+template <int I, typename R>
+__device__ __forceinline__ R feq_comp(R rho, R X, R Y, R ip) {
+    const R A = rho * ip, X2 = X * X, Y2 = Y * Y, Q = A * ip * X2 * Y2;
+    if (I == 0) return fma(rho, R(4.0 / 9.0), fma(R(-2.0 / 3.0) * A, X2 + Y2, Q));
+    if (I == 1 || I == 3) {
+        const R t = fma(R(2.0 / 3.0), X2, fma(R(-1.0 / 3.0), Y2, R(I == 1 ? -1.0 : 1.0) * X * Y2));
+        return R(0.5) * (fma(rho, fma(R(I == 1 ? 2.0 / 3.0 : -2.0 / 3.0), X, R(2.0 / 9.0)), fma(A, t, -Q)));
+    }
+    if (I == 2 || I == 4) {
+        const R t = fma(R(2.0 / 3.0), Y2, fma(R(-1.0 / 3.0), X2, R(I == 2 ? -1.0 : 1.0) * Y * X2));
+        return R(0.5) * (fma(rho, fma(R(I == 2 ? 2.0 / 3.0 : -2.0 / 3.0), Y, R(2.0 / 9.0)), fma(A, t, -Q)));
+    }
+    const double sx = (I == 5 || I == 8) ? 1.0 : -1.0, sy = (I == 5 || I == 6) ? 1.0 : -1.0;
+    const R XY = X * Y;
+    const R t = fma(R(1.0 / 3.0), X2 + Y2, fma(R(sx * sy), XY, XY * fma(R(sy), X, R(sx) * Y)));
+    return R(0.25) * (fma(rho, fma(R(1.0 / 3.0), fma(R(sx), X, R(sy) * Y), R(1.0 / 9.0)), fma(A, t, Q)));
+}
+
+// One component of the thermal equilibrium (Eq. 34).
+template <int I, typename R>
+__device__ __forceinline__ R geq_comp(R T, R X, R Y, R sigma, R cT2) {
+    if (I == 0) return T * (sigma - fma(X, X, fma(Y, Y, R(2) * cT2)));
+    const R u = (I == 1 || I == 3) ? X : Y;
+    return T * fma(R(0.5) * u, u, fma(R((I == 1 || I == 2) ? 0.5 : -0.5), u, R(0.5) * cT2));
+}
+
+template <int I>
+__device__ __forceinline__ void pull_one(const BufT<const __half>& B, const AuxT<float>& A, const KParamsT<float>& K,
+                                         const int (&o)[9], float (&f)[9], float (&g)[5], bool want_f, bool want_g) {
+    const Base s = load_base(B, A, K, o[I]);
+    const int Q = (int)K.g.plane;
+    if (want_f) f[I] = feq_comp<I>(s.rho, s.X, s.Y, s.ip) + __half2float(__ldg(B.f + I * Q + o[I]));
+    if (I < 5 && want_g)
+        g[I < 5 ? I : 0] = geq_comp<(I < 5 ? I : 0)>(s.T, s.X, s.Y, K.p.sigma, K.p.cT2) +
+                           __half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o[I]));
+}
+
 struct StoreH16N {
     using R = float;
     using S = __half;
+    static __device__ __forceinline__ void pull_all(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K,
+                                                    int x, int y, R (&f)[9], R (&g)[5], bool wf, bool wg) {
+        int o[9];
+        sources<int>(K.g, x, y, o);
+        pull_one<0>(B, A, K, o, f, g, wf, wg);
+        pull_one<1>(B, A, K, o, f, g, wf, wg);
+        pull_one<2>(B, A, K, o, f, g, wf, wg);
+        pull_one<3>(B, A, K, o, f, g, wf, wg);
+        pull_one<4>(B, A, K, o, f, g, wf, wg);
+        pull_one<5>(B, A, K, o, f, g, wf, wg);
+        pull_one<6>(B, A, K, o, f, g, wf, wg);
+        pull_one<7>(B, A, K, o, f, g, wf, wg);
+        pull_one<8>(B, A, K, o, f, g, wf, wg);
+    }
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
                                                  int y, R (&f)[9]) {
-        long long o[9];
-        sources(K.g, x, y, o);
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const Base s = load_base(B, A, K, o[i]);
-            R fe[9];
-            feq9(s.rho, s.X, s.Y, s.ip, fe);
-            f[i] = fe[i] + __half2float(__ldg(B.f + i * K.g.plane + o[i]));
-        }
+        R g[5];
+        pull_all(B, A, K, x, y, f, g, true, false);
     }
     static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
                                                  int y, R (&g)[5]) {
-        long long o[9];
-        sources(K.g, x, y, o);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) {
-            const Base s = load_base(B, A, K, o[i]);
-            R ge[5];
-            geq5(s.T, s.X, s.Y, K.p.sigma, K.p.cT2, ge);
-            g[i] = ge[i] + __half2float(__ldg(B.g + i * K.g.plane + o[i]));
-        }
+        R f[9];
+        pull_all(B, A, K, x, y, f, g, false, true);
+    }
+    static __device__ __forceinline__ void pull(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
+                                                int y, R (&f)[9], R (&g)[5]) {
+        pull_all(B, A, K, x, y, f, g, true, true);
     }
     // The record is rounded first and the baseline rebuilt from the rounded
     // halves, exactly as a reader will rebuild it.
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
                                                  const R (&f)[9], const R (&g)[5], R rho, R X, R Y, R T, R ip) {
-        const long long o = (long long)y * K.g.px + x;
+        const int o = y * K.g.px + x, Q = (int)K.g.plane;
         const __half2 a = __floats2half2_rn(rho - 1.0f, X);
         const __half2 b = __floats2half2_rn(Y, T - K.T0);
         uint2 r;
         r.x = *reinterpret_cast<const unsigned int*>(&a);
         r.y = *reinterpret_cast<const unsigned int*>(&b);
         B.rec[o] = r;
+        // same per-direction formulas, on the same rounded record, as pull_one
         const float2 fa = __half22float2(a), fb = __half22float2(b);
-        R fe[9], ge[5];
-        feq9(1.0f + fa.x, fa.y, fb.x, ip, fe);
-        geq5(K.T0 + fb.y, fa.y, fb.x, K.p.sigma, K.p.cT2, ge);
+        const float br = 1.0f + fa.x, bX = fa.y, bY = fb.x, bT = K.T0 + fb.y;
+        const float fe[9] = {feq_comp<0>(br, bX, bY, ip), feq_comp<1>(br, bX, bY, ip), feq_comp<2>(br, bX, bY, ip),
+                             feq_comp<3>(br, bX, bY, ip), feq_comp<4>(br, bX, bY, ip), feq_comp<5>(br, bX, bY, ip),
+                             feq_comp<6>(br, bX, bY, ip), feq_comp<7>(br, bX, bY, ip), feq_comp<8>(br, bX, bY, ip)};
+        const float s = K.p.sigma, c = K.p.cT2;
+        const float ge[5] = {geq_comp<0>(bT, bX, bY, s, c), geq_comp<1>(bT, bX, bY, s, c),
+                             geq_comp<2>(bT, bX, bY, s, c), geq_comp<3>(bT, bX, bY, s, c),
+                             geq_comp<4>(bT, bX, bY, s, c)};
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * K.g.plane + o] = __float2half_rn(f[i] - fe[i]);
+        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = __float2half_rn(f[i] - fe[i]);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * K.g.plane + o] = __float2half_rn(g[i] - ge[i]);
+        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = __float2half_rn(g[i] - ge[i]);
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
-        const float ip = __ldg(A.ip + (long long)y * K.g.px + x);
-        return coef_from_phi<FORCH>(1.0f / ip, ip, K);
+        const float ip = __ldg(A.ip + y * K.g.px + x);
+        return coef_from_phi<FORCH>(recip(ip), ip, K);
+    }
+    // Two interior nodes (x0, x0 + 1), x0 even.
+    template <int I>
+    static __device__ __forceinline__ void pull2_one(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K,
+                                                     const int (&o0)[9], const int (&o1)[9], f2 (&f)[9], f2 (&g)[5]) {
+        const int Q = (int)K.g.plane;
+        uint2 r0, r1;
+        float2 ip, df, dg = make_float2(0.0f, 0.0f);
+        if (column_dir(I)) {
+            const uint4 r = __ldg(reinterpret_cast<const uint4*>(B.rec + o0[I]));
+            r0 = make_uint2(r.x, r.y);
+            r1 = make_uint2(r.z, r.w);
+            ip = __ldg(reinterpret_cast<const float2*>(A.ip + o0[I]));
+            df = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.f + I * Q + o0[I])));
+            if (I < 5) dg = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.g + (I < 5 ? I : 0) * Q + o0[I])));
+        } else {
+            r0 = __ldg(B.rec + o0[I]);
+            r1 = __ldg(B.rec + o1[I]);
+            ip = make_float2(__ldg(A.ip + o0[I]), __ldg(A.ip + o1[I]));
+            df = make_float2(__half2float(__ldg(B.f + I * Q + o0[I])), __half2float(__ldg(B.f + I * Q + o1[I])));
+            if (I < 5)
+                dg = make_float2(__half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o0[I])),
+                                 __half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o1[I])));
+        }
+        const float2 a0 = __half22float2(*reinterpret_cast<const __half2*>(&r0.x));
+        const float2 b0 = __half22float2(*reinterpret_cast<const __half2*>(&r0.y));
+        const float2 a1 = __half22float2(*reinterpret_cast<const __half2*>(&r1.x));
+        const float2 b1 = __half22float2(*reinterpret_cast<const __half2*>(&r1.y));
+        const f2 rho = f2(1.0) + f2::make(a0.x, a1.x), X = f2::make(a0.y, a1.y), Y = f2::make(b0.x, b1.x);
+        const f2 ipp = f2::make(ip.x, ip.y);
+        f[I] = feq_comp<I>(rho, X, Y, ipp) + f2::make(df.x, df.y);
+        if (I < 5) {
+            const f2 T = f2(K.T0) + f2::make(b0.y, b1.y);
+            g[I < 5 ? I : 0] = geq_comp<(I < 5 ? I : 0)>(T, X, Y, f2(K.p.sigma), f2(K.p.cT2)) + f2::make(dg.x, dg.y);
+        }
+    }
+    static __device__ __forceinline__ void pull2(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x0,
+                                                 int y, f2 (&f)[9], f2 (&g)[5]) {
+        int o0[9], o1[9];
+        sources<int>(K.g, x0, y, o0);
+        sources<int>(K.g, x0 + 1, y, o1);
+        pull2_one<0>(B, A, K, o0, o1, f, g);
+        pull2_one<1>(B, A, K, o0, o1, f, g);
+        pull2_one<2>(B, A, K, o0, o1, f, g);
+        pull2_one<3>(B, A, K, o0, o1, f, g);
+        pull2_one<4>(B, A, K, o0, o1, f, g);
+        pull2_one<5>(B, A, K, o0, o1, f, g);
+        pull2_one<6>(B, A, K, o0, o1, f, g);
+        pull2_one<7>(B, A, K, o0, o1, f, g);
+        pull2_one<8>(B, A, K, o0, o1, f, g);
+    }
+    static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
+                                                  const f2 (&f)[9], const f2 (&g)[5], f2 rho, f2 X, f2 Y, f2 T, f2 ip) {
+        const int o = y * K.g.px + x0, Q = (int)K.g.plane;
+        const __half2 a0 = __floats2half2_rn(rho.lo() - 1.0f, X.lo()), b0 = __floats2half2_rn(Y.lo(), T.lo() - K.T0);
+        const __half2 a1 = __floats2half2_rn(rho.hi() - 1.0f, X.hi()), b1 = __floats2half2_rn(Y.hi(), T.hi() - K.T0);
+        uint4 r;
+        r.x = *reinterpret_cast<const unsigned int*>(&a0);
+        r.y = *reinterpret_cast<const unsigned int*>(&b0);
+        r.z = *reinterpret_cast<const unsigned int*>(&a1);
+        r.w = *reinterpret_cast<const unsigned int*>(&b1);
+        *reinterpret_cast<uint4*>(B.rec + o) = r;
+        const float2 fa0 = __half22float2(a0), fb0 = __half22float2(b0);
+        const float2 fa1 = __half22float2(a1), fb1 = __half22float2(b1);
+        const f2 br = f2(1.0) + f2::make(fa0.x, fa1.x), bX = f2::make(fa0.y, fa1.y), bY = f2::make(fb0.x, fb1.x);
+        const f2 bT = f2(K.T0) + f2::make(fb0.y, fb1.y);
+        const f2 fe[9] = {feq_comp<0>(br, bX, bY, ip), feq_comp<1>(br, bX, bY, ip), feq_comp<2>(br, bX, bY, ip),
+                          feq_comp<3>(br, bX, bY, ip), feq_comp<4>(br, bX, bY, ip), feq_comp<5>(br, bX, bY, ip),
+                          feq_comp<6>(br, bX, bY, ip), feq_comp<7>(br, bX, bY, ip), feq_comp<8>(br, bX, bY, ip)};
+        const f2 s = f2(K.p.sigma), c = f2(K.p.cT2);
+        const f2 ge[5] = {geq_comp<0>(bT, bX, bY, s, c), geq_comp<1>(bT, bX, bY, s, c), geq_comp<2>(bT, bX, bY, s, c),
+                          geq_comp<3>(bT, bX, bY, s, c), geq_comp<4>(bT, bX, bY, s, c)};
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const f2 d = f[i] - fe[i];
+            *reinterpret_cast<__half2*>(B.f + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+        }
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const f2 d = g[i] - ge[i];
+            *reinterpret_cast<__half2*>(B.g + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+        }
     }
 };
 
@@ -544,8 +829,7 @@ __device__ __forceinline__ void wall_state(const BufT<const typename P::S>& Bin,
     using R = typename P::R;
     const int sx = x + w.dx, sy = y + w.dy;
     R fs[9], gs[5];
-    P::pull9(Bin, A, K, sx, sy, fs);
-    P::pull5(Bin, A, K, sx, sy, gs);
+    P::pull(Bin, A, K, sx, sy, fs, gs);
     const Mom9T<R> ks = moments9(fs);
     const R Ts = sum5(gs) * K.p.inv_sigma;
     const CoefT<R> cs = P::template coef<FORCH>(A, K, sx, sy);
@@ -590,8 +874,7 @@ __device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin,
     using R = typename P::R;
     WallInfo w;
     if (!wall_info(K.g, K.b, x, y, w)) {
-        P::pull9(Bin, A, K, x, y, f);
-        P::pull5(Bin, A, K, x, y, g);
+        P::pull(Bin, A, K, x, y, f, g);
         k = moments9(f);
         n0 = sum5(g);
         T = n0 * K.p.inv_sigma;
@@ -605,13 +888,12 @@ __device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin,
 }
 
 // ---------------------------------------------------------------- kernels
+// One node's complete step: pull (or wall rebuild), macros, both collisions, store.
 template <class P, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(256) k_step(const BufT<typename P::S> in, const BufT<typename P::S> out,
-                                              const AuxT<typename P::R> A, const KParamsT<typename P::R> K) {
+__device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
+                                          const AuxT<typename P::R>& A, const KParamsT<typename P::R>& K, int x,
+                                          int y) {
     using R = typename P::R;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= K.g.nx || y >= K.g.ny) return;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
     R f[9], g[5];
     R rho, X, Y, T, Fx, Fy, n0;
@@ -620,6 +902,46 @@ __global__ void __launch_bounds__(256) k_step(const BufT<typename P::S> in, cons
     collide9<R, SHIFT>(f, k, rho, X, Y, Fx, Fy, c.ip, K.p);
     collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
     P::store(out, K, x, y, f, g, rho, X, Y, T, c.ip);
+}
+
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(256) k_step(const BufT<typename P::S> in, const BufT<typename P::S> out,
+                                              const AuxT<typename P::R> A, const KParamsT<typename P::R> K) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= K.g.nx || y >= K.g.ny) return;
+    step_node<P, SHIFT, FORCH>(in, out, A, K, x, y);
+}
+
+// FP16 forms, two nodes (x0, x0 + 1) per thread: interior pairs run the
+// collision on packed FP32 pairs; a pair with a wall node (or the odd last
+// column) falls back to the per-node path.  128-thread blocks capped at
+// 96 registers: 5 resident blocks (20 warps) per SM, no spills.
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, 5) k_step2(const BufT<typename P::S> in, const BufT<typename P::S> out,
+                                               const AuxT<float> A, const KParamsT<float> K) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= K.g.nx || y >= K.g.ny) return;
+    const bool has1 = x0 + 1 < K.g.nx;
+    WallInfo w;
+    if (!has1 || wall_info(K.g, K.b, x0, y, w) || wall_info(K.g, K.b, x0 + 1, y, w)) {
+        step_node<P, SHIFT, FORCH>(in, out, A, K, x0, y);
+        if (has1) step_node<P, SHIFT, FORCH>(in, out, A, K, x0 + 1, y);
+        return;
+    }
+    const PhysT<f2> P2 = splat(K.p);
+    const CoefT<f2> c = pack_coef(P::template coef<FORCH>(A, K, x0, y), P::template coef<FORCH>(A, K, x0 + 1, y));
+    f2 f[9], g[5];
+    P::pull2(as_const(in), A, K, x0, y, f, g);
+    const Mom9T<f2> k = moments9(f);
+    const f2 n0 = sum5(g);
+    const f2 T = n0 * P2.inv_sigma;
+    f2 X, Y, Fx, Fy;
+    macro_velocity<f2, FORCH>(k.rho, k.jx, k.jy, T, f2(A.ayg[y]), c, P2, X, Y, Fx, Fy);
+    collide9<f2, SHIFT>(f, k, k.rho, X, Y, Fx, Fy, c.ip, P2);
+    collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
+    P::store2(out, K, x0, y, f, g, k.rho, X, Y, T, c.ip);
 }
 
 // Macroscopic fields at the current time level (dense ny*nx FP64 outputs).
