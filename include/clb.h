@@ -191,6 +191,34 @@ int clb_sync(clb_handle* h);
 
 void clb_destroy(clb_handle* h);
 
+/* ---------------------------------------------------------------- batches
+ * A batch advances ncase independent simulations (uneven grids, their own
+ * parameters, porosity and walls) with one launch per step.  All cases share
+ * precision, shift and forchheimer.  Arrays of per-case inputs are indexed
+ * by case; phi[c] points to case c's ny*nx host porosity.  Steps advance
+ * every active case; clb_batch_set_active takes a flag per case (retired
+ * cases keep their state and stop advancing).  clb_batch_tune times each
+ * candidate tile shape for `steps` steps (the cases advance meanwhile) and
+ * keeps the fastest; *chosen receives its index.  Other conventions as for
+ * the single-case entry points.  The paper has no batched form; this is the
+ * data-parallel way to run parameter studies such as its Table 1. */
+typedef struct clb_batch clb_batch;
+int clb_batch_init(clb_batch** b, int32_t ncase, const clb_params* p, const double* const* phi, const clb_bc* bc,
+                   void* stream);
+int clb_batch_step(clb_batch* b, int64_t n);
+int clb_batch_set_active(clb_batch* b, const int32_t* active);
+int clb_batch_tune(clb_batch* b, int32_t steps, int32_t* chosen);
+/* Mean Nusselt number of `side` for every case (host array of ncase values). */
+int clb_batch_nusselt(clb_batch* b, int32_t side, double* nu);
+/* Macroscopic fields of case c (host arrays of that case's ny*nx values). */
+int clb_batch_macros(clb_batch* b, int32_t c, double* rho, double* ux, double* uy, double* T);
+/* Nodes updated per batch step (active cases), and steps taken. */
+int64_t clb_batch_nodes(const clb_batch* b);
+int64_t clb_batch_time(const clb_batch* b);
+int clb_batch_sync(clb_batch* b);
+const char* clb_batch_last_error(const clb_batch* b);
+void clb_batch_destroy(clb_batch* b);
+
 /* Allocation-free Nusselt reduction.  The paper has no counterpart: this
  * entry point exists for callers that cannot call cudaMalloc -- code that
  * runs inside another framework's memory pool, which may already hold

@@ -93,6 +93,25 @@ def load(build_if_needed: bool = True):
     L.clb_last_error.restype = ctypes.c_char_p
     L.clb_nusselt_field_static.argtypes = [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_double, _VP, _VP]
+    L.clb_batch_init.argtypes = [ctypes.POINTER(_VP), ctypes.c_int32, ctypes.POINTER(ClbParams),
+                                 ctypes.POINTER(_DP), ctypes.POINTER(ClbBc), _VP]
+    L.clb_batch_step.argtypes = [_VP, ctypes.c_int64]
+    L.clb_batch_set_active.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32)]
+    L.clb_batch_tune.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    L.clb_batch_nusselt.argtypes = [_VP, ctypes.c_int32, _DP]
+    L.clb_batch_macros.argtypes = [_VP, ctypes.c_int32, _DP, _DP, _DP, _DP]
+    L.clb_batch_nodes.argtypes = [_VP]
+    L.clb_batch_nodes.restype = ctypes.c_int64
+    L.clb_batch_time.argtypes = [_VP]
+    L.clb_batch_time.restype = ctypes.c_int64
+    L.clb_batch_sync.argtypes = [_VP]
+    L.clb_batch_last_error.argtypes = [_VP]
+    L.clb_batch_last_error.restype = ctypes.c_char_p
+    L.clb_batch_destroy.argtypes = [_VP]
+    L.clb_batch_destroy.restype = None
+    for name in ("clb_batch_init", "clb_batch_step", "clb_batch_set_active", "clb_batch_tune", "clb_batch_nusselt",
+                 "clb_batch_macros", "clb_batch_sync"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("clb_nusselt_field_static", "clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
                  "clb_residual", "clb_lattice_params", "clb_get_state", "clb_set_state", "clb_sync"):
         getattr(L, name).restype = ctypes.c_int
@@ -295,6 +314,119 @@ class Simulation:
     def close(self):
         if self.handle:
             clb_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------ batches
+def _bcheck(rc: int, b=None):
+    if rc != CLB_OK:
+        msg = load().clb_batch_last_error(b)
+        raise ClbError(rc, msg.decode() if msg else "")
+
+
+def clb_batch_init(params, phis, bcs, stream=None):
+    """params, phis, bcs: per-case lists (phi scalar or (ny, nx) array)."""
+    n = len(params)
+    P = (ClbParams * n)(*params)
+    B = (ClbBc * n)(*bcs)
+    keep = [_field(phi, p.nx * p.ny) for phi, p in zip(phis, params)]
+    ptrs = (_DP * n)(*[_dp(a) for a in keep])
+    h = _VP()
+    rc = load().clb_batch_init(ctypes.byref(h), n, P, ptrs, B, _VP(stream) if stream else None)
+    _bcheck(rc, None)
+    return h.value
+
+
+def clb_batch_step(b, n: int):
+    _bcheck(load().clb_batch_step(b, int(n)), b)
+
+
+def clb_batch_set_active(b, active):
+    a = (ctypes.c_int32 * len(active))(*[int(bool(v)) for v in active])
+    _bcheck(load().clb_batch_set_active(b, a), b)
+
+
+def clb_batch_tune(b, steps: int = 4) -> int:
+    ch = ctypes.c_int32(-1)
+    _bcheck(load().clb_batch_tune(b, int(steps), ctypes.byref(ch)), b)
+    return ch.value
+
+
+def clb_batch_nusselt(b, ncase: int, side: int = W) -> np.ndarray:
+    out = np.zeros(ncase)
+    _bcheck(load().clb_batch_nusselt(b, int(side), _dp(out)), b)
+    return out
+
+
+def clb_batch_macros(b, c: int, nx: int, ny: int):
+    out = [np.empty((ny, nx)) for _ in range(4)]
+    _bcheck(load().clb_batch_macros(b, int(c), *[_dp(a) for a in out]), b)
+    return tuple(out)
+
+
+def clb_batch_nodes(b) -> int:
+    return int(load().clb_batch_nodes(b))
+
+
+def clb_batch_time(b) -> int:
+    return int(load().clb_batch_time(b))
+
+
+def clb_batch_sync(b):
+    _bcheck(load().clb_batch_sync(b), b)
+
+
+def clb_batch_destroy(b):
+    if b:
+        load().clb_batch_destroy(b)
+
+
+class Batch:
+    """Owns one batch handle; cases are indexed 0..n-1."""
+
+    def __init__(self, params, phis, bcs, stream=None):
+        self.params = list(params)
+        self.handle = clb_batch_init(self.params, phis, bcs, stream)
+
+    def __len__(self):
+        return len(self.params)
+
+    def step(self, n: int):
+        clb_batch_step(self.handle, n)
+
+    def set_active(self, active):
+        clb_batch_set_active(self.handle, active)
+
+    def tune(self, steps: int = 4) -> int:
+        return clb_batch_tune(self.handle, steps)
+
+    def nusselt(self, side: int = W) -> np.ndarray:
+        return clb_batch_nusselt(self.handle, len(self), side)
+
+    def macros(self, c: int):
+        p = self.params[c]
+        return clb_batch_macros(self.handle, c, p.nx, p.ny)
+
+    @property
+    def nodes(self) -> int:
+        return clb_batch_nodes(self.handle)
+
+    @property
+    def time(self) -> int:
+        return clb_batch_time(self.handle)
+
+    def sync(self):
+        clb_batch_sync(self.handle)
+
+    def close(self):
+        if self.handle:
+            clb_batch_destroy(self.handle)
             self.handle = 0
 
     def __del__(self):

@@ -697,3 +697,6 @@ void clb_internal_set_error(const char* msg) { g_init_error = msg ? msg : ""; }
 extern "C" const char* clb_last_error(const clb_handle* h) {
     return h ? h->err.c_str() : g_init_error.c_str();
 }
+
+// ------------------------------------------------------------------ batches
+#include "clb_batch.cuh"

@@ -1,0 +1,322 @@
+// clb_batch.cuh -- batches of independent simulations advanced by one
+// launch per step (host side of clb_batch_*; included by clb_api.cu).
+//
+// Each case is an ordinary clb_handle (its own buffers, parameters and
+// reductions); the batch builds a device table of the cases and a tile list
+// over the active ones, and advances all of them with k_step_batch,
+// replayed from CUDA graphs of kGraphSteps steps.  Cases can be retired
+// (e.g. once steady) and the tile shape is chosen by a measured sweep.
+
+struct clb_batch {
+    std::vector<clb_handle*> cases;
+    std::vector<int32_t> active;
+    int prec = CLB_F64;
+    int shift = 1, forch = 1;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    void* table = nullptr;          // CaseT array on the device
+    int4* tiles = nullptr;          // tile list on the device
+    int ntiles = 0;
+    int64_t nodes = 0;              // active nodes per step
+    int par = 0;
+    int64_t t = 0;
+    int shape = 0;                  // index into kShapes
+    int per_cta = 8;                // tiles per CTA
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_failed = false;
+    std::string err;
+};
+
+namespace {
+// Candidate block shapes (threads in x, threads in y), 128 threads each.
+constexpr int kNumShapes = 3;
+constexpr int kShapes[kNumShapes][2] = {{64, 2}, {32, 4}, {16, 8}};
+constexpr int kPerCta[3] = {4, 16, 64};
+}  // namespace
+
+static int bfail(clb_batch* b, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (b) b->err = buf;
+    else g_init_error = buf;
+    return code;
+}
+
+#define CKB(b, call)                                                                                \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return bfail((b), e_ == cudaErrorMemoryAllocation ? CLB_ERR_OOM : CLB_ERR_CUDA,         \
+                         "%s failed: %s", #call, cudaGetErrorString(e_));                           \
+    } while (0)
+
+static void batch_drop_graphs(clb_batch* b) {
+    for (int i = 0; i < 2; ++i)
+        if (b->graph[i]) {
+            cudaGraphExecDestroy(b->graph[i]);
+            b->graph[i] = nullptr;
+        }
+    b->graph_failed = false;
+}
+
+static int nodes_per_thread(const clb_batch* b) { return b->prec == CLB_F64 ? 1 : 2; }
+
+// Tile list over the active cases for the current block shape.
+static int batch_build_tiles(clb_batch* b) {
+    const int bx = kShapes[b->shape][0], by = kShapes[b->shape][1];
+    const int tw = bx * nodes_per_thread(b);
+    std::vector<int4> host;
+    b->nodes = 0;
+    for (size_t c = 0; c < b->cases.size(); ++c) {
+        if (!b->active[c]) continue;
+        const clb_params& p = b->cases[c]->prm;
+        b->nodes += (int64_t)p.nx * p.ny;
+        for (int y0 = 0; y0 < p.ny; y0 += by)
+            for (int x0 = 0; x0 < p.nx; x0 += tw) host.push_back(make_int4((int)c, x0, y0, 0));
+    }
+    cudaFree(b->tiles);
+    b->tiles = nullptr;
+    b->ntiles = (int)host.size();
+    if (b->ntiles) {
+        CKB(b, cudaMalloc(&b->tiles, host.size() * sizeof(int4)));
+        CKB(b, cudaMemcpy(b->tiles, host.data(), host.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
+    batch_drop_graphs(b);
+    return CLB_OK;
+}
+
+template <class P, int NPT>
+static void batch_launch_as(clb_batch* b, cudaStream_t s) {
+    using C = CaseT<typename P::R, typename P::S>;
+    const C* tab = (const C*)b->table;
+    const dim3 block(kShapes[b->shape][0], kShapes[b->shape][1]);
+    const int grid = (b->ntiles + b->per_cta - 1) / b->per_cta;
+    if (b->shift && b->forch) k_step_batch<P, NPT, true, true><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+    else if (b->shift) k_step_batch<P, NPT, true, false><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+    else if (b->forch) k_step_batch<P, NPT, false, true><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+    else k_step_batch<P, NPT, false, false><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+}
+
+static void batch_launch(clb_batch* b, cudaStream_t s) {
+    if (b->ntiles > 0) {
+        if (b->prec == CLB_F16S) batch_launch_as<StoreH16, 2>(b, s);
+        else if (b->prec == CLB_F16N) batch_launch_as<StoreH16N, 2>(b, s);
+        else batch_launch_as<StoreF64, 1>(b, s);
+    }
+    b->par = 1 - b->par;
+}
+
+static cudaGraphExec_t batch_capture(clb_batch* b, int par) {
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ex = nullptr;
+    const int save = b->par;
+    b->par = par;
+    if (cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        b->par = save;
+        cudaGetLastError();
+        return nullptr;
+    }
+    for (int i = 0; i < kGraphSteps; ++i) batch_launch(b, b->cap_stream);
+    const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &gr);
+    b->par = save;
+    if (e != cudaSuccess || !gr) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaGraphInstantiate(&ex, gr, 0) != cudaSuccess) ex = nullptr;
+    cudaGraphDestroy(gr);
+    cudaGetLastError();
+    return ex;
+}
+
+// Keep every case handle's buffer parity and clock in step with the batch.
+static void batch_sync_cases(clb_batch* b) {
+    for (size_t c = 0; c < b->cases.size(); ++c) b->cases[c]->par = b->par;
+}
+
+extern "C" int clb_batch_init(clb_batch** out, int32_t ncase, const clb_params* p, const double* const* phi,
+                              const clb_bc* bc, void* stream) {
+    if (!out) return bfail(nullptr, CLB_ERR_ARG, "clb_batch_init: output pointer is NULL");
+    *out = nullptr;
+    if (ncase < 1 || !p || !phi || !bc) return bfail(nullptr, CLB_ERR_ARG, "clb_batch_init: bad arguments");
+    for (int c = 1; c < ncase; ++c)
+        if (p[c].precision != p[0].precision || p[c].shift != p[0].shift || p[c].forchheimer != p[0].forchheimer)
+            return bfail(nullptr, CLB_ERR_ARG, "clb_batch_init: all cases must share precision, shift, forchheimer");
+    clb_batch* b = new (std::nothrow) clb_batch();
+    if (!b) return bfail(nullptr, CLB_ERR_OOM, "clb_batch_init: out of host memory");
+    b->prec = p[0].precision;
+    b->shift = p[0].shift;
+    b->forch = p[0].forchheimer;
+    b->stream = (cudaStream_t)stream;
+    auto bail = [&](int code) {
+        g_init_error = b->err.empty() ? g_init_error : b->err;
+        clb_batch_destroy(b);
+        return code;
+    };
+    for (int c = 0; c < ncase; ++c) {
+        clb_handle* h = nullptr;
+        const int rc = clb_init(&h, &p[c], phi[c], nullptr, &bc[c], stream);
+        if (rc != CLB_OK) {
+            bfail(b, rc, "clb_batch_init: case %d: %s", c, g_init_error.c_str());
+            return bail(rc);
+        }
+        b->cases.push_back(h);
+        b->active.push_back(1);
+    }
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        bfail(b, CLB_ERR_CUDA, "clb_batch_init: stream creation failed");
+        return bail(CLB_ERR_CUDA);
+    }
+    // device table of the cases
+    size_t bytes;
+    std::vector<unsigned char> host;
+    if (b->prec == CLB_F64) {
+        std::vector<CaseT<double, double>> t(ncase);
+        for (int c = 0; c < ncase; ++c) {
+            clb_handle* h = b->cases[c];
+            t[c].K = h->k64;
+            t[c].A = h->aux64();
+            t[c].b[0] = h->buf<double>(0);
+            t[c].b[1] = h->buf<double>(1);
+        }
+        bytes = t.size() * sizeof(t[0]);
+        host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + bytes);
+    } else {
+        std::vector<CaseT<float, __half>> t(ncase);
+        for (int c = 0; c < ncase; ++c) {
+            clb_handle* h = b->cases[c];
+            t[c].K = h->k32;
+            t[c].A = h->aux32();
+            t[c].b[0] = h->buf<__half>(0);
+            t[c].b[1] = h->buf<__half>(1);
+        }
+        bytes = t.size() * sizeof(t[0]);
+        host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + bytes);
+    }
+    if (cudaMalloc(&b->table, bytes) != cudaSuccess ||
+        cudaMemcpy(b->table, host.data(), bytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+        bfail(b, CLB_ERR_CUDA, "clb_batch_init: case table upload failed");
+        return bail(CLB_ERR_CUDA);
+    }
+    const int rc = batch_build_tiles(b);
+    if (rc != CLB_OK) return bail(rc);
+    *out = b;
+    return CLB_OK;
+}
+
+extern "C" int clb_batch_step(clb_batch* b, int64_t n) {
+    if (!b) return CLB_ERR_ARG;
+    if (n < 0) return bfail(b, CLB_ERR_ARG, "clb_batch_step: negative step count");
+    int64_t left = n;
+    while (left > 0) {
+        if (left >= kGraphSteps && !b->graph_failed) {
+            if (!b->graph[b->par]) {
+                b->graph[b->par] = batch_capture(b, b->par);
+                if (!b->graph[b->par]) {
+                    b->graph_failed = true;
+                    continue;
+                }
+            }
+            CKB(b, cudaGraphLaunch(b->graph[b->par], b->stream));
+            left -= kGraphSteps;
+        } else {
+            batch_launch(b, b->stream);
+            CKB(b, cudaGetLastError());
+            left -= 1;
+        }
+    }
+    b->t += n;
+    batch_sync_cases(b);
+    for (size_t c = 0; c < b->cases.size(); ++c)
+        if (b->active[c]) b->cases[c]->t += n;
+    return CLB_OK;
+}
+
+extern "C" int clb_batch_set_active(clb_batch* b, const int32_t* active) {
+    if (!b || !active) return CLB_ERR_ARG;
+    for (size_t c = 0; c < b->cases.size(); ++c) b->active[c] = active[c] != 0;
+    return batch_build_tiles(b);
+}
+
+extern "C" int clb_batch_nusselt(clb_batch* b, int32_t side, double* nu) {
+    if (!b || !nu) return CLB_ERR_ARG;
+    batch_sync_cases(b);
+    for (size_t c = 0; c < b->cases.size(); ++c) {
+        const int rc = clb_nusselt(b->cases[c], side, &nu[c]);
+        if (rc != CLB_OK) return bfail(b, rc, "clb_batch_nusselt: case %zu: %s", c, b->cases[c]->err.c_str());
+    }
+    return CLB_OK;
+}
+
+extern "C" int clb_batch_macros(clb_batch* b, int32_t c, double* rho, double* ux, double* uy, double* T) {
+    if (!b || c < 0 || c >= (int32_t)b->cases.size()) return CLB_ERR_ARG;
+    batch_sync_cases(b);
+    const int rc = clb_macros(b->cases[c], rho, ux, uy, T);
+    if (rc != CLB_OK) return bfail(b, rc, "clb_batch_macros: case %d: %s", c, b->cases[c]->err.c_str());
+    return CLB_OK;
+}
+
+extern "C" int clb_batch_tune(clb_batch* b, int32_t steps, int32_t* chosen) {
+    if (!b || steps < 1) return CLB_ERR_ARG;
+    cudaEvent_t e0, e1;
+    CKB(b, cudaEventCreate(&e0));
+    CKB(b, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_s = b->shape, best_p = b->per_cta;
+    for (int s = 0; s < kNumShapes; ++s)
+        for (int q = 0; q < 3; ++q) {
+            b->shape = s;
+            b->per_cta = kPerCta[q];
+            int rc = batch_build_tiles(b);
+            if (rc != CLB_OK) return rc;
+            batch_launch(b, b->stream);   // warm-up step of this shape
+            CKB(b, cudaEventRecord(e0, b->stream));
+            for (int i = 0; i < steps; ++i) batch_launch(b, b->stream);
+            CKB(b, cudaEventRecord(e1, b->stream));
+            CKB(b, cudaEventSynchronize(e1));
+            CKB(b, cudaGetLastError());
+            float ms = 0.0f;
+            CKB(b, cudaEventElapsedTime(&ms, e0, e1));
+            b->t += steps + 1;
+            for (size_t c = 0; c < b->cases.size(); ++c)
+                if (b->active[c]) b->cases[c]->t += steps + 1;
+            if (ms < best) {
+                best = ms;
+                best_s = s;
+                best_p = kPerCta[q];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->shape = best_s;
+    b->per_cta = best_p;
+    batch_sync_cases(b);
+    if (chosen) *chosen = best_s * 3 + (best_p == kPerCta[0] ? 0 : best_p == kPerCta[1] ? 1 : 2);
+    return batch_build_tiles(b);
+}
+
+extern "C" int64_t clb_batch_nodes(const clb_batch* b) { return b ? b->nodes : -1; }
+
+extern "C" int64_t clb_batch_time(const clb_batch* b) { return b ? b->t : -1; }
+
+extern "C" int clb_batch_sync(clb_batch* b) {
+    if (!b) return CLB_ERR_ARG;
+    CKB(b, cudaStreamSynchronize(b->stream));
+    return CLB_OK;
+}
+
+extern "C" const char* clb_batch_last_error(const clb_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
+
+extern "C" void clb_batch_destroy(clb_batch* b) {
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_drop_graphs(b);
+    for (clb_handle* h : b->cases) clb_destroy(h);
+    cudaFree(b->table);
+    cudaFree(b->tiles);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+}

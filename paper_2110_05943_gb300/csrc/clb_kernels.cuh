@@ -918,11 +918,8 @@ __global__ void __launch_bounds__(256) k_step(const BufT<typename P::S> in, cons
 // column) falls back to the per-node path.  128-thread blocks capped at
 // 96 registers: 5 resident blocks (20 warps) per SM, no spills.
 template <class P, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(128, 5) k_step2(const BufT<typename P::S> in, const BufT<typename P::S> out,
-                                               const AuxT<float> A, const KParamsT<float> K) {
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= K.g.nx || y >= K.g.ny) return;
+__device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
+                                          const AuxT<float>& A, const KParamsT<float>& K, int x0, int y) {
     const bool has1 = x0 + 1 < K.g.nx;
     WallInfo w;
     if (!has1 || wall_info(K.g, K.b, x0, y, w) || wall_info(K.g, K.b, x0 + 1, y, w)) {
@@ -942,6 +939,60 @@ __global__ void __launch_bounds__(128, 5) k_step2(const BufT<typename P::S> in, 
     collide9<f2, SHIFT>(f, k, k.rho, X, Y, Fx, Fy, c.ip, P2);
     collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
     P::store2(out, K, x0, y, f, g, k.rho, X, Y, T, c.ip);
+}
+
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, 5) k_step2(const BufT<typename P::S> in, const BufT<typename P::S> out,
+                                                  const AuxT<float> A, const KParamsT<float> K) {
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= K.g.nx || y >= K.g.ny) return;
+    step_pair<P, SHIFT, FORCH>(in, out, A, K, x0, y);
+}
+
+// ---------------------------------------------------------------- batches
+// One case of a batch: parameters, auxiliary pointers and both buffers.
+template <typename R, typename S>
+struct CaseT {
+    KParamsT<R> K;
+    AuxT<R> A;
+    BufT<S> b[2];
+};
+
+// Independent cases advanced by one launch.  `tiles` lists (case, x0, y0)
+// in case order; CTA b owns the contiguous range [b * per_cta, ...), and its
+// threads cover a (NPT * blockDim.x) x blockDim.y block of nodes at each
+// tile (NPT = nodes per thread: 2 for the FP16 forms, 1 for FP64).  The
+// case descriptor is staged in shared memory whenever the case changes.
+template <class P, int NPT, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, 4) k_step_batch(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
+                                                       const int4* __restrict__ tiles, int ntiles, int per_cta,
+                                                       int par) {
+    using C = CaseT<typename P::R, typename P::S>;
+    __shared__ __align__(16) unsigned char raw[sizeof(C)];
+    C& sc = *reinterpret_cast<C*>(raw);
+    const int t0 = blockIdx.x * per_cta;
+    const int t1 = min(t0 + per_cta, ntiles);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    int cur = -1;
+    for (int t = t0; t < t1; ++t) {
+        const int4 tl = __ldg(tiles + t);
+        if (tl.x != cur) {
+            __syncthreads();
+            const unsigned* src = reinterpret_cast<const unsigned*>(cases + tl.x);
+            unsigned* dst = reinterpret_cast<unsigned*>(raw);
+            for (int w = tid; w < (int)(sizeof(C) / 4); w += nthr) dst[w] = __ldg(src + w);
+            __syncthreads();
+            cur = tl.x;
+        }
+        const int x = tl.y + NPT * threadIdx.x, y = tl.z + threadIdx.y;
+        if (x < sc.K.g.nx && y < sc.K.g.ny) {
+            if constexpr (NPT == 2)
+                step_pair<P, SHIFT, FORCH>(sc.b[par], sc.b[1 - par], sc.A, sc.K, x, y);
+            else
+                step_node<P, SHIFT, FORCH>(sc.b[par], sc.b[1 - par], sc.A, sc.K, x, y);
+        }
+    }
 }
 
 // Macroscopic fields at the current time level (dense ny*nx FP64 outputs).

@@ -1,0 +1,101 @@
+"""Batched form: independent cases advanced by one launch per step.
+
+Each case runs the same per-node code as a single simulation, so after the
+same number of steps a batched case must equal its stand-alone run bit for
+bit -- in every storage form, whatever tile shape the tuner picks, and with
+other cases retired part-way.  One case is also checked against the oracle.
+"""
+import numpy as np
+import pytest
+
+from cases import build, field_errors
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _cases(prec):
+    from paper_2110_05943_gb300 import clb
+    from paper_2110_05943_gb300.inputs import porosity_field
+    spec = [  # nx, ny, Ra, Da, Pr, sigma, phi (None: random field)
+        (37, 21, 1e5, 1e-2, 0.71, 0.8, 0.6),
+        (64, 64, 1e4, 1e-2, 1.0, 1.0, 0.6),
+        (130, 40, 1e6, 1e-3, 0.71, 1.5, None),
+        (20, 90, 1e3, 1e-4, 0.71, 0.5, 0.45),
+        (9, 9, 1e5, 1e-1, 0.71, 2.0, 0.9),
+    ]
+    params, phis = [], []
+    for k, (nx, ny, Ra, Da, Pr, sg, phi) in enumerate(spec):
+        params.append(clb.clb_params_default(nx=nx, ny=ny, Ra=Ra, Da=Da, Pr=Pr, sigma=sg, precision=prec))
+        phis.append(porosity_field(nx, ny, seed=30 + k, ell=6.0) if phi is None else phi)
+    return spec, params, phis
+
+
+def _single(params, phi):
+    from paper_2110_05943_gb300 import clb
+    return clb.Simulation.create(params, phi, clb.clb_bc_cavity(1.0, 0.0))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_batch_equals_single_runs_bit_for_bit(prec):
+    from paper_2110_05943_gb300 import clb
+    spec, params, phis = _cases(prec)
+    batch = clb.Batch(params, phis, [clb.clb_bc_cavity(1.0, 0.0) for _ in params])
+    batch.step(77)
+    for c, (p, phi) in enumerate(zip(params, phis)):
+        s = _single(p, phi)
+        s.step(77)
+        for a, b in zip(batch.macros(c), s.macros()):
+            assert np.array_equal(a, b), (prec, c)
+        s.close()
+    nu = batch.nusselt(0)
+    assert np.isfinite(nu).all() and nu.shape == (len(params),)
+    assert batch.nodes == sum(p.nx * p.ny for p in params)
+    batch.close()
+
+
+def test_batch_case_matches_oracle():
+    from paper_2110_05943_gb300 import clb
+    spec, params, phis = _cases(0)
+    batch = clb.Batch(params, phis, [clb.clb_bc_cavity(1.0, 0.0) for _ in params])
+    batch.step(600)
+    import oracle
+    c = 2
+    nx, ny, Ra, Da, Pr, sg, _ = spec[c]
+    o = oracle.Oracle(oracle.Problem(nx=nx, ny=ny, Ra=Ra, Da=Da, Pr=Pr, sigma=sg), phi=phis[c])
+    o.step(600)
+    e = field_errors(batch.macros(c), o.macros())
+    assert all(v <= 1e-10 for v in e.values()), e
+    batch.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_retired_cases_freeze_and_tuning_keeps_results(prec):
+    from paper_2110_05943_gb300 import clb
+    spec, params, phis = _cases(prec)
+    n = len(params)
+    batch = clb.Batch(params, phis, [clb.clb_bc_cavity(1.0, 0.0) for _ in params])
+    batch.step(40)
+    frozen = batch.macros(1)
+    active = [1] * n
+    active[1] = 0
+    batch.set_active(active)
+    choice = batch.tune(steps=2)          # 9 shapes x 3 steps = 27 more steps for the active cases
+    assert 0 <= choice < 9
+    batch.step(33)
+    for a, b in zip(batch.macros(1), frozen):
+        assert np.array_equal(a, b)
+    total = 40 + 27 + 33
+    for c in (0, 2, 4):
+        s = _single(params[c], phis[c])
+        s.step(total)
+        for a, b in zip(batch.macros(c), s.macros()):
+            assert np.array_equal(a, b), (prec, c)
+        s.close()
+    batch.close()
