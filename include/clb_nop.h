@@ -1,0 +1,86 @@
+/*
+ * clb_nop.h -- C ABI of the learned warm start's kernels: a small
+ * convolutional neural operator that predicts the steady (u, v, T) of a
+ * porous cavity from its porosity field and (Ra, Da, Pr, sigma), used to
+ * initialise the time march (clb_set_fields).  The paper has no learned
+ * component; the time march it describes still decides the answer.
+ *
+ * Conventions: all pointers are device pointers; activations are BF16 in
+ * NHWC layout (channels fastest); convolution weights are a BF16 matrix
+ * [taps * cin][cout] (cout fastest), taps = 9 for a 3x3 convolution with
+ * zero padding 1, 1 for a 1x1 convolution; biases, gradients of weights and
+ * optimiser state are FP32.  Every call is asynchronous on `stream`
+ * (cudaStream_t, NULL = legacy stream) and returns CLB_NOP_OK or an error;
+ * shapes are checked on the host before any launch.  Products run on the
+ * BF16 tensor cores with FP32 accumulation.
+ */
+#ifndef CLB_NOP_H
+#define CLB_NOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CLB_NOP_OK 0
+#define CLB_NOP_ERR_ARG (-1)
+#define CLB_NOP_ERR_CUDA (-2)
+
+/* y[n,h,w,co] = act(bias[co] + sum_{tap,ci} x[n,h+dy,w+dx,ci] W[tap*cin+ci][co]);
+ * act = ReLU if relu != 0; y is FP32 if y_f32 != 0, else BF16. */
+int clb_nop_conv_fwd(const void* x, const void* w, const float* bias, void* y, int32_t y_f32, int32_t relu,
+                     int32_t n, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps, void* stream);
+
+/* dx[n,h,w,ci] = sum_{tap,co} dy[n,h-dy,w-dx,co] W[tap*cin+ci][co], then
+ * zeroed where mask (the layer input, BF16) is <= 0 if mask != NULL. */
+int clb_nop_conv_dgrad(const void* dy, const void* w, const void* mask, void* dx, int32_t n, int32_t h, int32_t wd,
+                       int32_t cin, int32_t cout, int32_t taps, void* stream);
+
+/* dw[tap*cin+ci][co] += sum_{n,h,w} x[n,h+dy,w+dx,ci] dy[n,h,w,co]  (FP32
+ * atomics; clear dw first).  splitk >= 1 splits the pixel sum over blocks. */
+int clb_nop_conv_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t h, int32_t wd, int32_t cin,
+                       int32_t cout, int32_t taps, int32_t splitk, void* stream);
+
+/* db[c] += sum over npix pixels of dy[p][c]  (clear db first). */
+int clb_nop_bias_grad(const void* dy, float* db, int64_t npix, int32_t c, void* stream);
+
+/* 2x2 average pooling (h, w even): forward (n,h,w,c) -> (n,h/2,w/2,c);
+ * backward takes dy (n,h/2,w/2,c) and writes dx (n,h,w,c). */
+int clb_nop_pool2(const void* in, void* out, int32_t n, int32_t h, int32_t w, int32_t c, int32_t backward,
+                  void* stream);
+
+/* Nearest 2x upsampling: forward (n,h,w,c) -> (n,2h,2w,c); backward takes
+ * dy (n,2h,2w,c) and writes dx (n,h,w,c) (sum of the four copies). */
+int clb_nop_up2(const void* in, void* out, int32_t n, int32_t h, int32_t w, int32_t c, int32_t backward,
+                void* stream);
+
+/* Channel concatenation y = [a | b] over npix pixels; inverse != 0 splits y
+ * back into a and b. */
+int clb_nop_concat(void* a, void* b, void* y, int64_t npix, int32_t ca, int32_t cb, int32_t inverse, void* stream);
+
+/* Channel-weighted mean squared error of n FP32 values laid out with nch
+ * channels fastest (n a multiple of nch): *loss += sum_i w[i % nch]
+ * (pred_i - target_i)^2 / n and grad_i = 2 w[i % nch] (pred_i - target_i) / n
+ * in BF16; wch = NULL weighs every channel 1 (clear *loss first). */
+int clb_nop_mse(const float* pred, const float* target, const float* wch, int32_t nch, void* grad, float* loss,
+                int64_t n, void* stream);
+
+/* One Adam step (bias-corrected, step count t >= 1) on FP32 weights w with
+ * FP32 gradient g and moments m, v; wb (BF16 copy of w) refreshed if not NULL. */
+int clb_nop_adam(float* w, const float* g, float* m, float* v, void* wb, int64_t n, float lr, float b1, float b2,
+                 float eps, int32_t t, void* stream);
+
+/* out = (d1 + d2) where a > 0, else 0 (d2, a may be NULL: no term / no mask). */
+int clb_nop_add_mask(const void* d1, const void* d2, const void* a, void* out, int64_t n, void* stream);
+
+/* y = BF16(x) for n values. */
+int clb_nop_cast_bf16(const float* x, void* y, int64_t n, void* stream);
+
+/* Clear `bytes` bytes at ptr. */
+int clb_nop_zero(void* ptr, int64_t bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLB_NOP_H */

@@ -1,8 +1,9 @@
 """Build the CUDA library libclb.so in-tree for sm_103a (GB300).
 
-Two translation units (csrc/clb_api.cu includes the kernel headers;
-csrc/clb_static.cu is the allocation-free reduction), one -gencode, no
-cmake: a few seconds on either machine.
+Three translation units (csrc/clb_api.cu includes the LB kernel headers;
+csrc/clb_static.cu is the allocation-free reduction; csrc/nop_kernels.cu the
+warm-start network's kernels), one -gencode, no cmake: seconds on either
+machine.
 """
 from __future__ import annotations
 
@@ -15,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIB_DIR, "libclb.so")
-SOURCES = ["clb_api.cu", "clb_static.cu"]
+SOURCES = ["clb_api.cu", "clb_static.cu", "nop_kernels.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -28,7 +29,7 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
-    files.append(os.path.join(ROOT, "include", "clb.h"))
+    files += [os.path.join(ROOT, "include", h) for h in ("clb.h", "clb_nop.h")]
     return files
 
 
@@ -40,18 +41,32 @@ def up_to_date() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libclb.so if any source is newer; return its path."""
+    """Compile libclb.so if any source is newer; return its path.  The
+    translation units compile in parallel, then link once."""
     if not force and up_to_date():
         return LIB_PATH
     os.makedirs(LIB_DIR, exist_ok=True)
-    tmp = LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = [_nvcc(), ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), "-o", tmp]
-    cmd += [os.path.join(CSRC, s) for s in SOURCES]
+    tag = f"{os.getpid()}"
+    common = [_nvcc(), ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
+              "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
+        common.insert(1, "-Xptxas=-v")
+    objs, procs = [], []
+    for src in SOURCES:
+        obj = os.path.join(LIB_DIR, f"{os.path.splitext(src)[0]}.{tag}.o")
+        objs.append(obj)
+        procs.append(subprocess.Popen(common + ["-c", os.path.join(CSRC, src), "-o", obj]))
+    codes = [p.wait() for p in procs]
+    try:
+        if any(codes):
+            raise RuntimeError(f"nvcc failed for {[s for s, c in zip(SOURCES, codes) if c]}")
+        tmp = LIB_PATH + f".{tag}.tmp"
+        subprocess.run([_nvcc(), ARCH, "-shared", "-o", tmp] + objs, check=True)
+        os.replace(tmp, LIB_PATH)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB_PATH
 
 

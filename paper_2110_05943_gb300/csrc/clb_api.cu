@@ -188,21 +188,27 @@ static int map_params(const clb_params* p, clb_lattice* lat, std::string& why) {
     return CLB_OK;
 }
 
+// Block shapes: 128- (FP64) or 64-wide (FP16, two nodes per thread) rows for
+// coalescing; on small grids the blocks shrink (to 64 threads at least) until
+// there are two per SM, so a 128^2 cavity is not left on a third of the GPU.
+static void shape_blocks(int units, int ny, int bx, int threads, dim3& block, dim3& grid) {
+    const long long want = 2LL * 152;
+    while (bx > 32 && bx / 2 >= units) bx /= 2;
+    int by = threads / bx;
+    if (by > ny) by = ny < 1 ? 1 : ny;
+    auto count = [&](int a, int b) { return (long long)((units + a - 1) / a) * ((ny + b - 1) / b); };
+    while (count(bx, by) < want && bx * by > 64) {
+        if (by > 1) by /= 2;
+        else bx /= 2;
+    }
+    block = dim3(bx, by);
+    grid = dim3((units + bx - 1) / bx, (ny + by - 1) / by);
+}
+
 static void pick_launch(clb_handle* h) {
     const int nx = h->prm.nx, ny = h->prm.ny;
-    int bx = 128;
-    while (bx > 32 && bx / 2 >= nx) bx /= 2;
-    int by = 256 / bx;
-    if (by > ny) by = ny < 1 ? 1 : ny;
-    h->block = dim3(bx, by);
-    h->grid = dim3((nx + bx - 1) / bx, (ny + by - 1) / by);
-    const int npair = (nx + 1) / 2;
-    int bx2 = 64;
-    while (bx2 > 32 && bx2 / 2 >= npair) bx2 /= 2;
-    int by2 = 128 / bx2;
-    if (by2 > ny) by2 = ny < 1 ? 1 : ny;
-    h->block2 = dim3(bx2, by2);
-    h->grid2 = dim3((npair + bx2 - 1) / bx2, (ny + by2 - 1) / by2);
+    shape_blocks(nx, ny, 128, 256, h->block, h->grid);
+    shape_blocks((nx + 1) / 2, ny, 64, 128, h->block2, h->grid2);
 }
 
 static void free_all(clb_handle* h) {

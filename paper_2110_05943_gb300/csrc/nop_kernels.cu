@@ -1,0 +1,449 @@
+// nop_kernels.cu -- kernels of the learned warm start: a small convolutional
+// neural operator (U-Net-like) that maps (porosity field, Ra, Da, Pr, sigma)
+// to the steady (u, v, T) of the porous cavity, trained on steady states the
+// LB solver generates.  BF16 weights and activations, FP32 accumulation.
+//
+// Layout: activations NHWC (channels fastest), BF16.  Convolution weights
+// as a [taps * Cin][Cout] matrix (Cout fastest), taps = 9 (3x3) or 1 (1x1).
+// Every convolution pass is an implicit GEMM on the BF16 tensor cores
+// (mma.sync m16n8k16, FP32 accumulate): 64 x 64 output tiles, 32-deep K
+// chunks, four warps of 32 x 32, operands gathered into shared memory with
+// zero fill at image borders and tile tails.
+//   forward : Y[p, co]   = sum_{tap, ci} X[p + d(tap), ci] W[tap, ci, co] (+ b, ReLU)
+//   dgrad   : dX[p, ci]  = sum_{tap, co} dY[p - d(tap), co] W[tap, ci, co]
+//   wgrad   : dW[tap, ci, co] += sum_p X[p + d(tap), ci] dY[p, co]   (split K, FP32 atomics)
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/clb_nop.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+constexpr int kThreads = 128;
+
+enum Mode { FWD = 0, DGRAD = 1, WGRAD = 2 };
+
+struct ConvShape {
+    int n, h, w, cin, cout, taps;   // taps = 9 (3x3, padding 1) or 1 (1x1)
+};
+
+__device__ __forceinline__ int tap_dy(int t, int taps) { return taps == 9 ? t / 3 - 1 : 0; }
+__device__ __forceinline__ int tap_dx(int t, int taps) { return taps == 9 ? t % 3 - 1 : 0; }
+
+__device__ __forceinline__ uint32_t ld_pair(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// One 64 x 64 output tile over the K range [kb, kb + kchunk).  Index
+// arithmetic is 32-bit (the host rejects larger tensors).  The 64 rows' pixel
+// (FWD, DGRAD) or (tap, channel) (WGRAD) decompositions are computed once per
+// block; each thread keeps one K column (tid % 32) of both tiles, so its K
+// decomposition is computed once per chunk.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_conv_gemm(const __nv_bfloat16* __restrict__ A, const __nv_bfloat16* __restrict__ B,
+                                                        const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
+                                                        void* __restrict__ out, int out_f32, int relu, ConvShape s,
+                                                        int M, int N, int K, int kchunk) {
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];   // stored [n][k]
+    __shared__ int rb[BM], ry[BM], rx[BM];                      // per-row base / offsets, ry < -2 marks an empty row
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int kb = blockIdx.z * kchunk;
+    const int ke = kb + kchunk < K ? kb + kchunk : K;
+    const int hw = s.h * s.w;
+    if (tid < BM) {
+        const int m = m0 + tid;
+        if (m >= M) {
+            rb[tid] = 0; ry[tid] = -1000000; rx[tid] = 0;
+        } else if (MODE != WGRAD) {
+            const int n = m / hw, rem = m - n * hw, y = rem / s.w;
+            rb[tid] = n * s.h; ry[tid] = y; rx[tid] = rem - y * s.w;
+        } else {
+            const int tap = m / s.cin;
+            rb[tid] = m - tap * s.cin; ry[tid] = tap_dy(tap, s.taps); rx[tid] = tap_dx(tap, s.taps);
+        }
+    }
+    float acc[2][4][4];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
+    const int g = lane >> 2, tg = lane & 3;
+    const int col = tid & 31, row0 = tid >> 5;
+    const __nv_bfloat16 zero = __float2bfloat16(0.0f);
+    __syncthreads();
+    for (int k0 = kb; k0 < ke; k0 += BK) {
+        const int kk = k0 + col;
+        const bool kv = kk < ke;
+        if (MODE != WGRAD) {
+            // A = activations gathered at the tap's shift: k = tap * C + c
+            const int C = MODE == FWD ? s.cin : s.cout;
+            const int tap = kv ? kk / C : 0, c = kk - tap * C;
+            const int sg = MODE == FWD ? 1 : -1;
+            const int ddy = sg * tap_dy(tap, s.taps), ddx = sg * tap_dx(tap, s.taps);
+#pragma unroll 4
+            for (int j = 0; j < BM / 4; ++j) {
+                const int r = row0 + 4 * j;
+                const int yy = ry[r] + ddy, xx = rx[r] + ddx;
+                __nv_bfloat16 v = zero;
+                if (kv && yy >= 0 && yy < s.h && xx >= 0 && xx < s.w) v = A[((rb[r] + yy) * s.w + xx) * C + c];
+                As[r][col] = v;
+            }
+            // B = weights; FWD: W[k][n], DGRAD: W[tap * cin + n][co] with k = tap * cout + co
+            const int t2 = MODE == DGRAD && kv ? kk / s.cout : 0, co = kk - t2 * s.cout;
+#pragma unroll 4
+            for (int j = 0; j < BN / 4; ++j) {
+                const int nn = row0 + 4 * j, n = n0 + nn;
+                __nv_bfloat16 v = zero;
+                if (kv && n < N) v = MODE == FWD ? B[kk * s.cout + n] : B[(t2 * s.cin + n) * s.cout + co];
+                Bs[nn][col] = v;
+            }
+        } else {
+            // k = pixel: A = X at the row's tap shift, channel rb[r]; B = dY[pixel][n]
+            const int n = kv ? kk / hw : 0, rem = kk - n * hw, y = rem / s.w, x = rem - (rem / s.w) * s.w;
+#pragma unroll 4
+            for (int j = 0; j < BM / 4; ++j) {
+                const int r = row0 + 4 * j;
+                const int yy = y + ry[r], xx = x + rx[r];
+                __nv_bfloat16 v = zero;
+                if (kv && yy >= 0 && yy < s.h && xx >= 0 && xx < s.w) v = A[((n * s.h + yy) * s.w + xx) * s.cin + rb[r]];
+                As[r][col] = v;
+            }
+#pragma unroll 4
+            for (int j = 0; j < BN / 4; ++j) {
+                const int nn = row0 + 4 * j, c = n0 + nn;
+                Bs[nn][col] = kv && c < N ? B[kk * s.cout + c] : zero;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < BK; ks += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm + i * 16 + g;
+                af[i][0] = ld_pair(&As[r][ks + tg * 2]);
+                af[i][1] = ld_pair(&As[r + 8][ks + tg * 2]);
+                af[i][2] = ld_pair(&As[r][ks + tg * 2 + 8]);
+                af[i][3] = ld_pair(&As[r + 8][ks + tg * 2 + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int c = wn + j * 8 + g;
+                bf[j][0] = ld_pair(&Bs[c][ks + tg * 2]);
+                bf[j][1] = ld_pair(&Bs[c][ks + tg * 2 + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma16816(acc[i][j], af[i], bf[j]);
+        }
+        __syncthreads();
+    }
+    // epilogue: element (row, col) of each 16 x 8 accumulator tile
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int row = m0 + wm + i * 16 + g + (r >= 2 ? 8 : 0);
+                const int cc = n0 + wn + j * 8 + tg * 2 + (r & 1);
+                if (row >= M || cc >= N) continue;
+                float v = acc[i][j][r];
+                const int o = row * N + cc;
+                if (MODE == WGRAD) {
+                    atomicAdd(reinterpret_cast<float*>(out) + o, v);
+                    continue;
+                }
+                if (bias) v += bias[cc];
+                if (relu) v = v > 0.0f ? v : 0.0f;
+                if (mask && !(__bfloat162float(mask[o]) > 0.0f)) v = 0.0f;
+                if (out_f32) reinterpret_cast<float*>(out)[o] = v;
+                else reinterpret_cast<__nv_bfloat16*>(out)[o] = __float2bfloat16(v);
+            }
+}
+
+template <int MODE>
+int launch_gemm(const void* A, const void* B, const float* bias, const void* mask, void* out, int out_f32, int relu,
+                ConvShape s, long long M, long long N, long long K, int splitk, cudaStream_t st) {
+    if (M <= 0 || N <= 0 || K <= 0) return CLB_NOP_ERR_ARG;
+    // every element index of every operand must fit in 32 bits
+    const long long npix = (long long)s.n * s.h * s.w;
+    const long long cmax = s.cin > s.cout ? s.cin : s.cout;
+    if (npix * cmax * s.taps >= 2147483647LL || M * N >= 2147483647LL) return CLB_NOP_ERR_ARG;
+    const long long gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
+    if (gn > 65535) return CLB_NOP_ERR_ARG;
+    if (splitk < 1) splitk = 1;
+    long long kchunk = (K + splitk - 1) / splitk;
+    kchunk = (kchunk + BK - 1) / BK * BK;
+    const long long gz = (K + kchunk - 1) / kchunk;
+    if (gz > 65535) return CLB_NOP_ERR_ARG;
+    k_conv_gemm<MODE><<<dim3((unsigned)gm, (unsigned)gn, (unsigned)gz), kThreads, 0, st>>>(
+        (const __nv_bfloat16*)A, (const __nv_bfloat16*)B, bias, (const __nv_bfloat16*)mask, out, out_f32, relu, s,
+        (int)M, (int)N, (int)K, (int)kchunk);
+    return cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+}
+
+bool bad_shape(int n, int h, int w, int cin, int cout, int taps) {
+    return n < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (taps != 1 && taps != 9);
+}
+
+// ---------------------------------------------------------------- elementwise
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dy, float* __restrict__ db, long long npix, int c) {
+    // one block per 256 pixels x all channels: per-channel partial sums, atomics
+    const long long p0 = (long long)blockIdx.x * 256;
+    for (int ch = threadIdx.x; ch < c; ch += blockDim.x) {
+        float s = 0.0f;
+        const long long p1 = p0 + 256 < npix ? p0 + 256 : npix;
+        for (long long p = p0; p < p1; ++p) s += __bfloat162float(dy[p * c + ch]);
+        atomicAdd(db + ch, s);
+    }
+}
+
+__global__ void k_pool2_fwd(const __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ y, int n, int h, int w, int c) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ho = h / 2, wo = w / 2;
+    if (i >= (long long)n * ho * wo * c) return;
+    const int ch = (int)(i % c);
+    long long p = i / c;
+    const int xo = (int)(p % wo);
+    p /= wo;
+    const int yo = (int)(p % ho);
+    const int b = (int)(p / ho);
+    const long long base = (((long long)b * h + 2 * yo) * w + 2 * xo) * c + ch;
+    const float s = __bfloat162float(x[base]) + __bfloat162float(x[base + c]) + __bfloat162float(x[base + (long long)w * c]) +
+                    __bfloat162float(x[base + (long long)w * c + c]);
+    y[i] = __float2bfloat16(0.25f * s);
+}
+
+__global__ void k_pool2_bwd(const __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dx, int n, int h, int w, int c) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * h * w * c) return;
+    const int ch = (int)(i % c);
+    long long p = i / c;
+    const int x = (int)(p % w);
+    p /= w;
+    const int y = (int)(p % h);
+    const int b = (int)(p / h);
+    const int ho = h / 2, wo = w / 2;
+    dx[i] = __float2bfloat16(0.25f * __bfloat162float(dy[(((long long)b * ho + y / 2) * wo + x / 2) * c + ch]));
+}
+
+__global__ void k_up2_fwd(const __nv_bfloat16* __restrict__ x, __nv_bfloat16* __restrict__ y, int n, int h, int w, int c) {
+    // x: (n, h, w, c) -> y: (n, 2h, 2w, c), nearest
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int H = 2 * h, W = 2 * w;
+    if (i >= (long long)n * H * W * c) return;
+    const int ch = (int)(i % c);
+    long long p = i / c;
+    const int X = (int)(p % W);
+    p /= W;
+    const int Y = (int)(p % H);
+    const int b = (int)(p / H);
+    y[i] = x[(((long long)b * h + Y / 2) * w + X / 2) * c + ch];
+}
+
+__global__ void k_up2_bwd(const __nv_bfloat16* __restrict__ dy, __nv_bfloat16* __restrict__ dx, int n, int h, int w, int c) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * h * w * c) return;
+    const int ch = (int)(i % c);
+    long long p = i / c;
+    const int x = (int)(p % w);
+    p /= w;
+    const int y = (int)(p % h);
+    const int b = (int)(p / h);
+    const int W = 2 * w;
+    const long long base = (((long long)b * 2 * h + 2 * y) * W + 2 * x) * c + ch;
+    const float s = __bfloat162float(dy[base]) + __bfloat162float(dy[base + c]) + __bfloat162float(dy[base + (long long)W * c]) +
+                    __bfloat162float(dy[base + (long long)W * c + c]);
+    dx[i] = __float2bfloat16(s);
+}
+
+// Channel concatenation of a (npix, ca) and b (npix, cb) into y (npix, ca + cb), and its inverse.
+__global__ void k_concat(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __restrict__ b, __nv_bfloat16* __restrict__ y,
+                         long long npix, int ca, int cb, int inverse) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = ca + cb;
+    if (i >= npix * c) return;
+    const long long p = i / c;
+    const int ch = (int)(i - p * c);
+    if (!inverse) y[i] = ch < ca ? a[p * ca + ch] : b[p * cb + ch - ca];
+    else if (ch < ca) const_cast<__nv_bfloat16*>(a)[p * ca + ch] = y[i];
+    else const_cast<__nv_bfloat16*>(b)[p * cb + ch - ca] = y[i];
+}
+
+// Channel-weighted mean squared error over n values (nch channels, fastest
+// index): loss += sum_i w[c] (pred_i - target_i)^2 / n, grad_i = 2 w[c]
+// (pred_i - target_i) / n as BF16; w = NULL means all weights 1.
+__global__ void k_mse(const float* __restrict__ pred, const float* __restrict__ target, const float* __restrict__ wch,
+                      int nch, __nv_bfloat16* __restrict__ grad, float* __restrict__ loss, long long n) {
+    __shared__ float sh[32];
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float e = 0.0f;
+    if (i < n) {
+        const float wc = wch ? wch[i % nch] : 1.0f;
+        const float d = pred[i] - target[i];
+        grad[i] = __float2bfloat16(2.0f * wc * d / (float)n);
+        e = wc * d * d / (float)n;
+    }
+    for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = e;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        e = threadIdx.x < blockDim.x / 32 ? sh[threadIdx.x] : 0.0f;
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_down_sync(0xffffffffu, e, o);
+        if (threadIdx.x == 0) atomicAdd(loss, e);
+    }
+}
+
+// Adam on FP32 master weights; refreshes the BF16 working copy.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       __nv_bfloat16* __restrict__ wb, long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16(wi);
+}
+
+__global__ void k_cast_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = __float2bfloat16(x[i]);
+}
+
+unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
+
+int status() { return cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" int clb_nop_conv_fwd(const void* x, const void* w, const float* bias, void* y, int32_t y_f32, int32_t relu,
+                                int32_t n, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                                void* stream) {
+    if (!x || !w || !y || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
+    const ConvShape s{n, h, wd, cin, cout, taps};
+    return launch_gemm<FWD>(x, w, bias, nullptr, y, y_f32, relu, s, (long long)n * h * wd, cout, (long long)taps * cin, 1,
+                            (cudaStream_t)stream);
+}
+
+extern "C" int clb_nop_conv_dgrad(const void* dy, const void* w, const void* mask, void* dx, int32_t n, int32_t h,
+                                  int32_t wd, int32_t cin, int32_t cout, int32_t taps, void* stream) {
+    if (!dy || !w || !dx || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
+    const ConvShape s{n, h, wd, cin, cout, taps};
+    return launch_gemm<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, (long long)n * h * wd, cin, (long long)taps * cout, 1,
+                              (cudaStream_t)stream);
+}
+
+extern "C" int clb_nop_conv_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t h, int32_t wd,
+                                  int32_t cin, int32_t cout, int32_t taps, int32_t splitk, void* stream) {
+    if (!x || !dy || !dw || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
+    const ConvShape s{n, h, wd, cin, cout, taps};
+    return launch_gemm<WGRAD>(x, dy, nullptr, nullptr, dw, 1, 0, s, (long long)taps * cin, cout, (long long)n * h * wd,
+                              splitk, (cudaStream_t)stream);
+}
+
+extern "C" int clb_nop_bias_grad(const void* dy, float* db, int64_t npix, int32_t c, void* stream) {
+    if (!dy || !db || npix < 1 || c < 1) return CLB_NOP_ERR_ARG;
+    k_bias_grad<<<(unsigned)((npix + 255) / 256), 128, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)dy, db, npix, c);
+    return status();
+}
+
+extern "C" int clb_nop_pool2(const void* in, void* out, int32_t n, int32_t h, int32_t w, int32_t c, int32_t backward,
+                             void* stream) {
+    if (!in || !out || n < 1 || h < 2 || w < 2 || c < 1 || (h & 1) || (w & 1)) return CLB_NOP_ERR_ARG;
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (!backward)
+        k_pool2_fwd<<<nblk((long long)n * (h / 2) * (w / 2) * c), 256, 0, st>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, n, h, w, c);
+    else
+        k_pool2_bwd<<<nblk((long long)n * h * w * c), 256, 0, st>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, n, h, w, c);
+    return status();
+}
+
+extern "C" int clb_nop_up2(const void* in, void* out, int32_t n, int32_t h, int32_t w, int32_t c, int32_t backward,
+                           void* stream) {
+    if (!in || !out || n < 1 || h < 1 || w < 1 || c < 1) return CLB_NOP_ERR_ARG;
+    const cudaStream_t st = (cudaStream_t)stream;
+    if (!backward)
+        k_up2_fwd<<<nblk((long long)n * 4 * h * w * c), 256, 0, st>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, n, h, w, c);
+    else
+        k_up2_bwd<<<nblk((long long)n * h * w * c), 256, 0, st>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, n, h, w, c);
+    return status();
+}
+
+extern "C" int clb_nop_concat(void* a, void* b, void* y, int64_t npix, int32_t ca, int32_t cb, int32_t inverse,
+                              void* stream) {
+    if (!a || !b || !y || npix < 1 || ca < 1 || cb < 1) return CLB_NOP_ERR_ARG;
+    k_concat<<<nblk(npix * (ca + cb)), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)a, (const __nv_bfloat16*)b,
+                                                                        (__nv_bfloat16*)y, npix, ca, cb, inverse);
+    return status();
+}
+
+extern "C" int clb_nop_mse(const float* pred, const float* target, const float* wch, int32_t nch, void* grad,
+                           float* loss, int64_t n, void* stream) {
+    if (!pred || !target || !grad || !loss || n < 1 || nch < 1 || n % nch) return CLB_NOP_ERR_ARG;
+    k_mse<<<nblk(n), 256, 0, (cudaStream_t)stream>>>(pred, target, wch, nch, (__nv_bfloat16*)grad, loss, n);
+    return status();
+}
+
+extern "C" int clb_nop_adam(float* w, const float* g, float* m, float* v, void* wb, int64_t n, float lr, float b1,
+                            float b2, float eps, int32_t t, void* stream) {
+    if (!w || !g || !m || !v || n < 1 || t < 1) return CLB_NOP_ERR_ARG;
+    float c1 = 1.0f, c2 = 1.0f, p1 = 1.0f, p2 = 1.0f;
+    for (int i = 0; i < t && i < 100000; ++i) {
+        p1 *= b1;
+        p2 *= b2;
+    }
+    c1 = 1.0f - p1;
+    c2 = 1.0f - p2;
+    k_adam<<<nblk(n), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, (__nv_bfloat16*)wb, n, lr, b1, b2, eps, c1, c2);
+    return status();
+}
+
+extern "C" int clb_nop_cast_bf16(const float* x, void* y, int64_t n, void* stream) {
+    if (!x || !y || n < 1) return CLB_NOP_ERR_ARG;
+    k_cast_bf16<<<nblk(n), 256, 0, (cudaStream_t)stream>>>(x, (__nv_bfloat16*)y, n);
+    return status();
+}
+
+extern "C" int clb_nop_zero(void* ptr, int64_t bytes, void* stream) {
+    if (!ptr || bytes < 0) return CLB_NOP_ERR_ARG;
+    return cudaMemsetAsync(ptr, 0, (size_t)bytes, (cudaStream_t)stream) == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+}
+
+namespace {
+__global__ void k_add_mask(const __nv_bfloat16* __restrict__ d1, const __nv_bfloat16* __restrict__ d2,
+                           const __nv_bfloat16* __restrict__ a, __nv_bfloat16* __restrict__ out, long long n) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = __bfloat162float(d1[i]);
+    if (d2) v += __bfloat162float(d2[i]);
+    if (a && !(__bfloat162float(a[i]) > 0.0f)) v = 0.0f;
+    out[i] = __float2bfloat16(v);
+}
+}  // namespace
+
+extern "C" int clb_nop_add_mask(const void* d1, const void* d2, const void* a, void* out, int64_t n, void* stream) {
+    if (!d1 || !out || n < 1) return CLB_NOP_ERR_ARG;
+    k_add_mask<<<nblk(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)d1, (const __nv_bfloat16*)d2,
+                                                          (const __nv_bfloat16*)a, (__nv_bfloat16*)out, n);
+    return status();
+}

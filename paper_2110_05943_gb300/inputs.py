@@ -121,3 +121,22 @@ def batch_cases(n: int = 512, seed: int = 7, side_lo: int = 64, side_hi: int = 1
         out.append(CavityCase(nx=nx, ny=ny, Ra=10 ** rng.uniform(3, 6), Da=10 ** rng.uniform(-4, -1),
                               Pr=pr, phi=rng.uniform(0.4, 0.9), sigma=rng.uniform(0.5, 2.0)))
     return out
+
+
+def warmstart_cases(n: int = 2200, seed: int = 11, size: int = 128, ell: float = 16.0, amp: float = 0.1,
+                    pr_lo: float = 0.7, pr_hi: float = 1.0):
+    """Seeded square cavities for the learned warm start: log10 Ra in [3, 6],
+    log10 Da in [-4, -1], mean porosity in [0.4, 0.9], sigma in [0.5, 2],
+    Pr uniform in [pr_lo, pr_hi]; each case has its own porosity field
+    eps(x) = clip(mean + amp * g(x), 0.3, 0.95), g a unit Gaussian random
+    field (correlation length ell) with seed seed * 100003 + case index.
+    Returns a list of (CavityCase, (size, size) porosity field)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        ra, da = 10 ** rng.uniform(3, 6), 10 ** rng.uniform(-4, -1)
+        mean, sg, pr = rng.uniform(0.4, 0.9), rng.uniform(0.5, 2.0), rng.uniform(pr_lo, pr_hi)
+        g = gaussian_random_field(size, size, ell, seed * 100003 + i)
+        phi = np.ascontiguousarray(np.clip(mean + amp * g, 0.3, 0.95))
+        out.append((CavityCase(nx=size, ny=size, Ra=ra, Da=da, Pr=pr, phi=mean, sigma=sg), phi))
+    return out

@@ -1,5 +1,5 @@
 """The C ABI library builds for sm_103a, loads without a GPU, and exports
-every entry point include/clb.h declares (no compute calls here)."""
+every entry point include/*.h declares (no compute calls here)."""
 import ctypes
 import os
 import re
@@ -7,15 +7,19 @@ import re
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "clb.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b(clb_[a-z_]+)\s*\(", src))
+def _declared(header=None):
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h") or (header and h != header):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names |= set(re.findall(r"\b(clb_[a-z0-9_]+)\s*\(", src))
     return sorted(names)
 
 
 def test_header_declares_the_boundary():
-    names = _declared()
+    names = _declared("clb.h")
     for n in ("clb_init", "clb_step", "clb_macros", "clb_nusselt", "clb_residual", "clb_destroy",
               "clb_get_state", "clb_set_state", "clb_last_error"):
         assert n in names
@@ -57,3 +61,21 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu():
     mixed = clb.clb_bc(("wall", "periodic", "wall", "wall"))
     with pytest.raises(clb.ClbError):
         clb.clb_init(p, np.full(256, 0.5), mixed)
+
+
+def test_surrogate_entry_points_declared_and_reject_bad_shapes():
+    """The learned warm start's kernels (include/clb_nop.h) are exported and
+    validate shapes on the host before any launch."""
+    from paper_2110_05943_gb300 import surrogate
+    names = _declared("clb_nop.h")
+    for n in ("clb_nop_conv_fwd", "clb_nop_conv_dgrad", "clb_nop_conv_wgrad", "clb_nop_adam", "clb_nop_mse"):
+        assert n in names
+    lib = surrogate._lib()
+    fake = ctypes.c_void_p(16)          # never dereferenced: the calls fail validation first
+    assert lib.clb_nop_conv_fwd(fake, fake, None, fake, 0, 1, 1, 8, 8, 4, 4, 5, None) == -1      # taps 5
+    assert lib.clb_nop_conv_fwd(fake, fake, None, fake, 0, 1, 0, 8, 8, 4, 4, 9, None) == -1      # n = 0
+    assert lib.clb_nop_conv_fwd(None, fake, None, fake, 0, 1, 1, 8, 8, 4, 4, 9, None) == -1      # null x
+    # 32-bit index guard: 2^16 x 2^16 pixels x 1 channel x 9 taps
+    assert lib.clb_nop_conv_fwd(fake, fake, None, fake, 0, 1, 1, 65536, 65536, 1, 1, 9, None) == -1
+    assert lib.clb_nop_pool2(fake, fake, 1, 7, 8, 4, 0, None) == -1                            # odd height
+    assert lib.clb_nop_adam(fake, fake, fake, fake, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == -1  # t = 0
