@@ -17,6 +17,12 @@ is the same metric through the public C ABI from pinned host buffers:
 clb_init (porosity upload) + K steps + clb_macros (four fields back) +
 clb_nusselt, wall-clock.  `--impl reference` times the FP64 CPU oracle on
 the host cores on a bounded sample of the same workload.
+
+Secondary objects on the same line: `forms` (FP16-storage forms at 8192^2),
+`batch` (512 seeded cavities in one launch per step), `cpu_baseline`,
+`steady_state` (time to steady state of each form on the Table 1 case) and
+`warm_start` (FP64 march from rest vs from the learned warm start on held-out
+cavities).  `--no-forms/--no-batch/--no-cpu/--no-steady/--no-warm` skip them.
 """
 from __future__ import annotations
 
@@ -313,6 +319,40 @@ def batched_form(clb, torch, args, hbm_peak, src):
                            "steps_f16n": res[2][1], "seconds_f64": res[0][2], "seconds_f16n": res[2][2]}}
 
 
+def warm_start_form(clb, torch, ncase=4):
+    """The learned warm start with the committed weights on the first `ncase`
+    held-out 128^2 cavities (warmstart_cases seed 11, indices 2000...): FP64
+    march from rest and from the network's prediction to max(r_u, r_T) <= 1e-8
+    over 100-step intervals; steps, wall time (inference included), the step
+    after which Nu stays within 1e-4 of the cold run's converged value, and
+    the final Nusselt numbers."""
+    from paper_2110_05943_gb300 import surrogate, warmstart
+    from paper_2110_05943_gb300.inputs import warmstart_cases
+    wpath = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2110_05943_gb300", "weights",
+                         "warmstart_128.npz")
+    net = surrogate.Net.create(torch, seed=0).load(wpath)
+    stream = torch.cuda.current_stream().cuda_stream
+    rows = []
+    for c, phi in warmstart_cases(2000 + ncase, seed=11)[2000:]:
+        t0 = time.perf_counter()
+        init = surrogate.warm_fields(net, phi, c.Ra, c.Da, c.Pr, c.sigma)
+        torch.cuda.synchronize()
+        t_inf = time.perf_counter() - t0
+        sc, tc, nc, okc, hc = warmstart.march(c, phi, None, stream, torch=torch)
+        sw, tw, nw, okw, hw = warmstart.march(c, phi, init, stream, torch=torch)
+        rows.append({"Ra": round(c.Ra, 1), "Da": float(f"{c.Da:.4g}"), "steps_cold": sc, "steps_warm": sw,
+                     "sec_cold": round(tc, 3), "sec_warm": round(tw + t_inf, 3),
+                     "steps_nu_1e-4_cold": warmstart.steps_to_nu(hc, nc),
+                     "steps_nu_1e-4_warm": warmstart.steps_to_nu(hw, nc),
+                     "nu_cold": nc, "nu_warm": nw, "rel_nu": abs(nw / nc - 1), "converged": bool(okc and okw)})
+    ok = [r for r in rows if r["converged"]]
+    return {"workload": f"first {ncase} held-out 128x128 warm-start cavities, FP64 march, committed weights",
+            "criterion": "max(r_u, r_T) <= 1e-8 over 100-step intervals",
+            "steps_ratio_total": (sum(r["steps_warm"] for r in ok) / sum(r["steps_cold"] for r in ok)) if ok else None,
+            "wall_speedup_total": (sum(r["sec_cold"] for r in ok) / sum(r["sec_warm"] for r in ok)) if ok else None,
+            "max_rel_nu": max((r["rel_nu"] for r in ok), default=None), "cases": rows}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -440,6 +480,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_oracle_rate(phi)
     if not args.no_steady:
         line["steady_state"] = steady_state_forms(clb, torch)
+    if not args.no_warm and ws == 1:
+        line["warm_start"] = warm_start_form(clb, torch)
     print(json.dumps(line), flush=True)
 
 
@@ -454,6 +496,7 @@ def main():
     ap.add_argument("--no-steady", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16-storage forms at 8192^2")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-case batch")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--size", type=int, default=4096, help="grid side (default 4096; smaller for profiling)")
     ap.add_argument("--precision", choices=("f64", "f16s", "f16n"), default="f64",
                     help="storage form of the main measurement (default f64, the reported workload)")
