@@ -12,7 +12,11 @@
  * optimiser state are FP32.  Every call is asynchronous on `stream`
  * (cudaStream_t, NULL = legacy stream) and returns CLB_NOP_OK or an error;
  * shapes are checked on the host before any launch.  Products run on the
- * BF16 tensor cores with FP32 accumulation.
+ * BF16 tensor cores with FP32 accumulation: the forward and input-gradient
+ * convolutions on tcgen05 (accumulator in TMEM) whenever the gathered
+ * operand's channel count is a multiple of 8 and the operands are 16-byte
+ * aligned (for the forward pass: when the transposed weights are given),
+ * otherwise, and for the weight gradient, on mma.sync.
  */
 #ifndef CLB_NOP_H
 #define CLB_NOP_H
@@ -26,11 +30,15 @@ extern "C" {
 #define CLB_NOP_OK 0
 #define CLB_NOP_ERR_ARG (-1)
 #define CLB_NOP_ERR_CUDA (-2)
+#define CLB_NOP_ERR_TIMEOUT (-3)
 
 /* y[n,h,w,co] = act(bias[co] + sum_{tap,ci} x[n,h+dy,w+dx,ci] W[tap*cin+ci][co]);
- * act = ReLU if relu != 0; y is FP32 if y_f32 != 0, else BF16. */
-int clb_nop_conv_fwd(const void* x, const void* w, const float* bias, void* y, int32_t y_f32, int32_t relu,
-                     int32_t n, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps, void* stream);
+ * act = ReLU if relu != 0; y is FP32 if y_f32 != 0, else BF16.  wt, if not
+ * NULL, is W transposed ([cout][taps*cin], clb_nop_transpose) and enables
+ * the tcgen05 path. */
+int clb_nop_conv_fwd(const void* x, const void* w, const void* wt, const float* bias, void* y, int32_t y_f32,
+                     int32_t relu, int32_t n, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
+                     void* stream);
 
 /* dx[n,h,w,ci] = sum_{tap,co} dy[n,h-dy,w-dx,co] W[tap*cin+ci][co], then
  * zeroed where mask (the layer input, BF16) is <= 0 if mask != NULL. */
@@ -38,7 +46,8 @@ int clb_nop_conv_dgrad(const void* dy, const void* w, const void* mask, void* dx
                        int32_t cin, int32_t cout, int32_t taps, void* stream);
 
 /* dw[tap*cin+ci][co] += sum_{n,h,w} x[n,h+dy,w+dx,ci] dy[n,h,w,co]  (FP32
- * atomics; clear dw first).  splitk >= 1 splits the pixel sum over blocks. */
+ * atomics; clear dw first).  splitk >= 1 splits the pixel sum over that many
+ * blocks; splitk <= 0 lets the library choose (about four blocks per SM). */
 int clb_nop_conv_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t h, int32_t wd, int32_t cin,
                        int32_t cout, int32_t taps, int32_t splitk, void* stream);
 
@@ -76,6 +85,14 @@ int clb_nop_add_mask(const void* d1, const void* d2, const void* a, void* out, i
 
 /* y = BF16(x) for n values. */
 int clb_nop_cast_bf16(const float* x, void* y, int64_t n, void* stream);
+
+/* wt[c][r] = w[r][c] for a BF16 rows x cols matrix. */
+int clb_nop_transpose(const void* w, void* wt, int32_t rows, int32_t cols, void* stream);
+
+/* Synchronises `stream` and reports (and clears) the tcgen05 kernels'
+ * time-out flag: CLB_NOP_ERR_TIMEOUT if a kernel gave up waiting for its
+ * tensor-core operations (about 2 s) and skipped its output. */
+int clb_nop_check(void* stream);
 
 /* Clear `bytes` bytes at ptr. */
 int clb_nop_zero(void* ptr, int64_t bytes, void* stream);

@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/clb_nop.h"
 
 namespace {
@@ -186,7 +188,7 @@ int launch_gemm(const void* A, const void* B, const float* bias, const void* mas
     if (npix * cmax * s.taps >= 2147483647LL || M * N >= 2147483647LL) return CLB_NOP_ERR_ARG;
     const long long gm = (M + BM - 1) / BM, gn = (N + BN - 1) / BN;
     if (gn > 65535) return CLB_NOP_ERR_ARG;
-    if (splitk < 1) splitk = 1;
+    if (splitk < 1) splitk = (int)std::max(1LL, std::min(64LL, K / 4096));   // automatic (weight gradient)
     long long kchunk = (K + splitk - 1) / splitk;
     kchunk = (kchunk + BK - 1) / BK * BK;
     const long long gz = (K + kchunk - 1) / kchunk;
@@ -199,6 +201,415 @@ int launch_gemm(const void* A, const void* B, const float* bias, const void* mas
 
 bool bad_shape(int n, int h, int w, int cin, int cout, int taps) {
     return n < 1 || h < 1 || w < 1 || cin < 1 || cout < 1 || (taps != 1 && taps != 9);
+}
+
+// ---------------------------------------------------------------- tcgen05 path
+// Forward and input-gradient convolutions on the 5th-generation tensor cores
+// when the gathered operand's channel count is a multiple of 8 (so 8
+// consecutive K indices are 8 contiguous channels of one tap: one 16-byte
+// vector).  One CTA per 128-pixel x tile_n output tile; 64-deep K chunks are
+// gathered by all 128 threads into double-buffered shared memory in the
+// canonical K-major layout without swizzle (8-row x 16-byte core matrices,
+// 128 B apart along K and 1024 B apart along M/N); thread 0 issues four
+// tcgen05.mma (M 128, N tile_n, K 16, BF16 x BF16 -> FP32) per chunk and
+// commits them to the buffer's mbarrier; the FP32 accumulator lives in TMEM
+// and each warp reads its 32 lanes back with tcgen05.ld for the epilogue.
+constexpr int TC_M = 128, TC_K = 64, TC_THREADS = 128;
+constexpr int TC_A_BYTES = TC_M * TC_K * 2;                  // 16 KiB per A buffer
+constexpr long long TC_TIMEOUT_CYCLES = 4000000000LL;        // ~2 s at 2 GHz
+
+__device__ unsigned int g_nop_timeout = 0;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Shared-memory matrix descriptor: start address, leading (K) and stride
+// (M/N) byte offsets, descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           (1ull << 46);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulate, BF16 A and B, both
+// K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__device__ __forceinline__ uint32_t tc_idesc(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t a) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+}
+
+// Waits for completion `parity` of the mbarrier; false after the time limit.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.test_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > TC_TIMEOUT_CYCLES) return false;
+    }
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+        : "r"(taddr)
+        : "memory");
+}
+
+// MODE FWD: A = activations X (C = cin), B = W^T [cout][taps * cin].
+// MODE DGRAD: A = output gradient dY (C = cout), B = W [taps * cin][cout]
+// read as B^T[ci][tap * cout + co].
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __nv_bfloat16* __restrict__ A,
+                                                        const __nv_bfloat16* __restrict__ B,
+                                                        const float* __restrict__ bias,
+                                                        const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
+                                                        int out_f32, int relu, ConvShape s, int M, int N, int K,
+                                                        int tile_n, int tmem_cols, int vec_out) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int b_bytes = tile_n * TC_K * 2;
+    unsigned char* const a_base = smem;                       // two A buffers, TC_A_BYTES apart
+    unsigned char* const b_base = smem + 2 * TC_A_BYTES;      // two B buffers, b_bytes apart
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * TC_A_BYTES + 2 * b_bytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * tile_n;
+    const int nt = min(tile_n, N - n0);                 // live columns of this tile
+    const int ntp = (nt + 15) & ~15;                    // MMA N (multiple of 16)
+    const int C = MODE == FWD ? s.cin : s.cout;
+    const int sg = MODE == FWD ? 1 : -1;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]));
+        mbar_init(smem_u32(&mbar[1]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // this thread's A row: pixel m0 + tid
+    const int m = m0 + tid;
+    int rb = 0, ry = -1000000, rx = 0;
+    if (m < M) {
+        const int hw = s.h * s.w, n = m / hw, rem = m - n * hw;
+        ry = rem / s.w;
+        rx = rem - ry * s.w;
+        rb = n * s.h;
+    }
+    const uint32_t idesc = tc_idesc(ntp);
+    const int nchunks = (K + TC_K - 1) / TC_K;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+        const int bi = c & 1;
+        if (c >= 2 && ok) ok = mbar_wait(smem_u32(&mbar[bi]), ((c - 2) >> 1) & 1);
+        const int k0 = c * TC_K;
+        // A: row tid, eight 16-byte K vectors
+#pragma unroll
+        for (int kv = 0; kv < 8; ++kv) {
+            const int k = k0 + 8 * kv;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (k < K) {
+                const int tap = k / C, ch = k - tap * C;
+                const int yy = ry + sg * tap_dy(tap, s.taps), xx = rx + sg * tap_dx(tap, s.taps);
+                if (yy >= 0 && yy < s.h && xx >= 0 && xx < s.w)
+                    v = __ldg(reinterpret_cast<const uint4*>(A + ((rb + yy) * s.w + xx) * C + ch));
+            }
+            *reinterpret_cast<uint4*>(a_base + bi * TC_A_BYTES + (tid >> 3) * 1024 + kv * 128 + (tid & 7) * 16) = v;
+        }
+        // B: ntp rows, eight 16-byte K vectors each
+        for (int e = tid; e < ntp * 8; e += TC_THREADS) {
+            const int r = e % ntp, kv = e / ntp, k = k0 + 8 * kv, gn = n0 + r;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (r < nt && k < K) {
+                if (MODE == FWD) {
+                    v = __ldg(reinterpret_cast<const uint4*>(B + gn * K + k));
+                } else {
+                    const int tap = k / s.cout, co = k - tap * s.cout;
+                    v = __ldg(reinterpret_cast<const uint4*>(B + (tap * s.cin + gn) * s.cout + co));
+                }
+            }
+            *reinterpret_cast<uint4*>(b_base + bi * b_bytes + (r >> 3) * 1024 + kv * 128 + (r & 7) * 16) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(a_base + bi * TC_A_BYTES), b0 = smem_u32(b_base + bi * b_bytes);
+#pragma unroll
+            for (int ks = 0; ks < TC_K / 16; ++ks)
+                tc_mma(tmem, tc_desc(a0 + ks * 256, 128, 1024), tc_desc(b0 + ks * 256, 128, 1024), idesc,
+                       (c > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(smem_u32(&mbar[bi]));
+        }
+    }
+    // every thread waits for the last commit (it covers all earlier MMAs)
+    if (ok) ok = mbar_wait(smem_u32(&mbar[(nchunks - 1) & 1]), ((nchunks - 1) >> 1) & 1);
+    // a thread that timed out earlier skipped its waits but not the barriers;
+    // agree on the outcome before touching TMEM
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < ntp; c0 += 8) {
+            uint32_t r[8];
+            tc_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row < M) {
+                const int o = row * N + n0 + c0;
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    v[j] = __uint_as_float(r[j]);
+                    if (bias && c0 + j < nt) v[j] += bias[n0 + c0 + j];
+                    if (relu) v[j] = v[j] > 0.0f ? v[j] : 0.0f;
+                }
+                if (c0 + 8 <= nt && vec_out) {
+                    // eight consecutive outputs of this row: one 16-byte (BF16) or two (FP32) stores
+                    if (mask) {
+                        const uint4 mk = *reinterpret_cast<const uint4*>(mask + o);
+                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (!(__bfloat162float(mb[j]) > 0.0f)) v[j] = 0.0f;
+                    }
+                    if (out_f32) {
+                        float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+                        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    } else {
+                        uint4 pk;
+                        __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = pk;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (c0 + j >= nt) break;
+                        float x = v[j];
+                        if (mask && !(__bfloat162float(mask[o + j]) > 0.0f)) x = 0.0f;
+                        if (out_f32) reinterpret_cast<float*>(out)[o + j] = x;
+                        else reinterpret_cast<__nv_bfloat16*>(out)[o + j] = __float2bfloat16(x);
+                    }
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(&g_nop_timeout, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// Weight gradient on tcgen05: D[m = tap * cin + ci][n = co] = sum over pixels
+// p of X[p + d(tap)][ci] dY[p][co], K = pixels, split over gridDim.z CTAs
+// (FP32 atomics into dw).  Both operands are staged MN-major: a core matrix
+// is 8 pixels (K) x 8 consecutive channels (16 bytes, M or N), exactly one
+// global 16-byte vector per row; core matrices are 128 B apart along M/N
+// (stride byte offset) and 128 * (rows / 8) B apart along K (leading byte
+// offset).  Requires cin % 8 == 0 and cout % 8 == 0.
+__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __restrict__ X,
+                                                         const __nv_bfloat16* __restrict__ dY, float* __restrict__ dw,
+                                                         ConvShape s, int M, int N, int npix, int kchunk, int tile_n,
+                                                         int tmem_cols) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int b_bytes = tile_n * TC_K * 2;
+    unsigned char* const a_base = smem;
+    unsigned char* const b_base = smem + 2 * TC_A_BYTES;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * TC_A_BYTES + 2 * b_bytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * tile_n;
+    const int nt = min(tile_n, N - n0), ntp = (nt + 15) & ~15;
+    const int kb = blockIdx.z * kchunk, ke = min(kb + kchunk, npix);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]));
+        mbar_init(smem_u32(&mbar[1]));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    // A rows: 16 groups of 8 channels, group g = (m0 / 8 + g): tap and channel
+    const int hw = s.h * s.w;
+    const int kl = tid & 63;                  // this thread's pixel within a chunk
+    const int g0 = tid >> 6;                  // its first channel group (then every second one)
+    const uint32_t idesc = tc_idesc(ntp) | (1u << 15) | (1u << 16);     // A and B MN-major
+    const int lbo_a = 128 * (TC_M / 8), lbo_b = 128 * (ntp / 8);
+    const int nchunks = (ke - kb + TC_K - 1) / TC_K;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+        const int bi = c & 1;
+        if (c >= 2 && ok) ok = mbar_wait(smem_u32(&mbar[bi]), ((c - 2) >> 1) & 1);
+        const int p = kb + c * TC_K + kl;
+        int pn = 0, py = -1000000, px = 0;
+        if (p < ke) {
+            pn = p / hw;
+            const int rem = p - pn * hw;
+            py = rem / s.w;
+            px = rem - py * s.w;
+        }
+        unsigned char* const ab = a_base + bi * TC_A_BYTES + (kl >> 3) * lbo_a + (kl & 7) * 16;
+#pragma unroll
+        for (int j = 0; j < TC_M / 16; ++j) {
+            const int g = g0 + 2 * j, m = m0 + 8 * g;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (m < M) {
+                const int tap = m / s.cin, ci = m - tap * s.cin;
+                const int yy = py + tap_dy(tap, s.taps), xx = px + tap_dx(tap, s.taps);
+                if (yy >= 0 && yy < s.h && xx >= 0 && xx < s.w)
+                    v = __ldg(reinterpret_cast<const uint4*>(X + ((pn * s.h + yy) * s.w + xx) * s.cin + ci));
+            }
+            *reinterpret_cast<uint4*>(ab + g * 128) = v;
+        }
+        unsigned char* const bb = b_base + bi * b_bytes + (kl >> 3) * lbo_b + (kl & 7) * 16;
+        for (int g = g0; g < ntp / 8; g += 2) {
+            const int n = n0 + 8 * g;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (p < ke && 8 * g < nt) v = __ldg(reinterpret_cast<const uint4*>(dY + p * s.cout + n));
+            *reinterpret_cast<uint4*>(bb + g * 128) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(a_base + bi * TC_A_BYTES), b0 = smem_u32(b_base + bi * b_bytes);
+#pragma unroll
+            for (int ks = 0; ks < TC_K / 16; ++ks)
+                tc_mma(tmem, tc_desc(a0 + ks * 2 * lbo_a, lbo_a, 128), tc_desc(b0 + ks * 2 * lbo_b, lbo_b, 128),
+                       idesc, (c > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(smem_u32(&mbar[bi]));
+        }
+    }
+    if (ok && nchunks > 0) ok = mbar_wait(smem_u32(&mbar[(nchunks - 1) & 1]), ((nchunks - 1) >> 1) & 1);
+    ok = __syncthreads_and(ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && nchunks > 0) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < ntp; c0 += 8) {
+            uint32_t r[8];
+            tc_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (c0 + j >= nt) break;
+                    atomicAdd(dw + row * N + n0 + c0 + j, __uint_as_float(r[j]));
+                }
+            }
+        }
+    } else if (!ok && tid == 0) {
+        atomicExch(&g_nop_timeout, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// Launches the tcgen05 kernel; false when the shape is not one it takes.
+template <int MODE>
+bool launch_tc(const void* A, const void* B, const float* bias, const void* mask, void* out, int out_f32, int relu,
+               ConvShape s, long long M, long long N, long long K, cudaStream_t st, int* rc) {
+    const int C = MODE == FWD ? s.cin : s.cout;
+    if (C % 8 || !aligned16(A) || !aligned16(B) || M <= 0 || N <= 0 || K <= 0) return false;
+    const long long npix = (long long)s.n * s.h * s.w;
+    const long long cmax = s.cin > s.cout ? s.cin : s.cout;
+    if (npix * cmax * s.taps >= 2147483647LL || M * N >= 2147483647LL) return false;
+    const int tile_n = N <= 256 ? (int)((N + 15) & ~15LL) : 256;
+    int cols = 32;
+    while (cols < tile_n) cols <<= 1;
+    const size_t smem = 2 * (size_t)TC_A_BYTES + 2 * (size_t)tile_n * TC_K * 2 + 32;
+    if (cudaFuncSetAttribute(k_conv_tc<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * TC_A_BYTES + 2 * 256 * TC_K * 2 + 32) != cudaSuccess) {
+        *rc = CLB_NOP_ERR_CUDA;
+        return true;
+    }
+    const dim3 grid((unsigned)((M + TC_M - 1) / TC_M), (unsigned)((N + tile_n - 1) / tile_n));
+    // 16-byte epilogue stores: rows of N outputs stay 16-byte aligned when N % 8 == 0
+    const int vec_out = N % 8 == 0 && aligned16(out) && (!mask || aligned16(mask));
+    k_conv_tc<MODE><<<grid, TC_THREADS, smem, st>>>((const __nv_bfloat16*)A, (const __nv_bfloat16*)B, bias,
+                                                    (const __nv_bfloat16*)mask, out, out_f32, relu, s, (int)M, (int)N,
+                                                    (int)K, tile_n, cols, vec_out);
+    *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+    return true;
+}
+
+// Launches the tcgen05 weight gradient; false when the shape is not one it takes.
+bool launch_wgrad_tc(const void* x, const void* dy, float* dw, ConvShape s, int splitk, cudaStream_t st, int* rc) {
+    if (s.cin % 8 || s.cout % 8 || !aligned16(x) || !aligned16(dy)) return false;
+    const long long npix = (long long)s.n * s.h * s.w;
+    const long long cmax = s.cin > s.cout ? s.cin : s.cout;
+    const long long M = (long long)s.taps * s.cin, N = s.cout;
+    if (npix * cmax * s.taps >= 2147483647LL || M * N >= 2147483647LL) return false;
+    const int tile_n = N <= 256 ? (int)((N + 15) & ~15LL) : 256;
+    int cols = 32;
+    while (cols < tile_n) cols <<= 1;
+    const long long tiles = ((M + TC_M - 1) / TC_M) * ((N + tile_n - 1) / tile_n);
+    if (splitk < 1) {
+        // automatic: about four CTAs per SM, each with at least 8 K chunks
+        const long long want = (4LL * 152 + tiles - 1) / tiles, most = (npix + 8 * TC_K - 1) / (8 * TC_K);
+        splitk = (int)std::max(1LL, std::min(want, most));
+    }
+    long long kchunk = (npix + splitk - 1) / splitk;
+    kchunk = (kchunk + TC_K - 1) / TC_K * TC_K;
+    const long long gz = (npix + kchunk - 1) / kchunk;
+    if (gz > 65535) return false;
+    const size_t smem = 2 * (size_t)TC_A_BYTES + 2 * (size_t)tile_n * TC_K * 2 + 32;
+    if (cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             2 * TC_A_BYTES + 2 * 256 * TC_K * 2 + 32) != cudaSuccess) {
+        *rc = CLB_NOP_ERR_CUDA;
+        return true;
+    }
+    const dim3 grid((unsigned)((M + TC_M - 1) / TC_M), (unsigned)((N + tile_n - 1) / tile_n), (unsigned)gz);
+    k_wgrad_tc<<<grid, TC_THREADS, smem, st>>>((const __nv_bfloat16*)x, (const __nv_bfloat16*)dy, dw, s, (int)M,
+                                               (int)N, (int)npix, (int)kchunk, tile_n, cols);
+    *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+    return true;
 }
 
 // ---------------------------------------------------------------- elementwise
@@ -336,27 +747,34 @@ int status() { return cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_E
 }  // namespace
 
 // ---------------------------------------------------------------- C ABI
-extern "C" int clb_nop_conv_fwd(const void* x, const void* w, const float* bias, void* y, int32_t y_f32, int32_t relu,
-                                int32_t n, int32_t h, int32_t wd, int32_t cin, int32_t cout, int32_t taps,
-                                void* stream) {
+extern "C" int clb_nop_conv_fwd(const void* x, const void* w, const void* wt, const float* bias, void* y,
+                                int32_t y_f32, int32_t relu, int32_t n, int32_t h, int32_t wd, int32_t cin,
+                                int32_t cout, int32_t taps, void* stream) {
     if (!x || !w || !y || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
     const ConvShape s{n, h, wd, cin, cout, taps};
-    return launch_gemm<FWD>(x, w, bias, nullptr, y, y_f32, relu, s, (long long)n * h * wd, cout, (long long)taps * cin, 1,
-                            (cudaStream_t)stream);
+    const long long M = (long long)n * h * wd, K = (long long)taps * cin;
+    int rc;
+    if (wt && launch_tc<FWD>(x, wt, bias, nullptr, y, y_f32, relu, s, M, cout, K, (cudaStream_t)stream, &rc))
+        return rc;
+    return launch_gemm<FWD>(x, w, bias, nullptr, y, y_f32, relu, s, M, cout, K, 1, (cudaStream_t)stream);
 }
 
 extern "C" int clb_nop_conv_dgrad(const void* dy, const void* w, const void* mask, void* dx, int32_t n, int32_t h,
                                   int32_t wd, int32_t cin, int32_t cout, int32_t taps, void* stream) {
     if (!dy || !w || !dx || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
     const ConvShape s{n, h, wd, cin, cout, taps};
-    return launch_gemm<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, (long long)n * h * wd, cin, (long long)taps * cout, 1,
-                              (cudaStream_t)stream);
+    const long long M = (long long)n * h * wd, K = (long long)taps * cout;
+    int rc;
+    if (launch_tc<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, K, (cudaStream_t)stream, &rc)) return rc;
+    return launch_gemm<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, K, 1, (cudaStream_t)stream);
 }
 
 extern "C" int clb_nop_conv_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t h, int32_t wd,
                                   int32_t cin, int32_t cout, int32_t taps, int32_t splitk, void* stream) {
     if (!x || !dy || !dw || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
     const ConvShape s{n, h, wd, cin, cout, taps};
+    int rc;
+    if (launch_wgrad_tc(x, dy, dw, s, splitk, (cudaStream_t)stream, &rc)) return rc;
     return launch_gemm<WGRAD>(x, dy, nullptr, nullptr, dw, 1, 0, s, (long long)taps * cin, cout, (long long)n * h * wd,
                               splitk, (cudaStream_t)stream);
 }
@@ -446,4 +864,29 @@ extern "C" int clb_nop_add_mask(const void* d1, const void* d2, const void* a, v
     k_add_mask<<<nblk(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)d1, (const __nv_bfloat16*)d2,
                                                           (const __nv_bfloat16*)a, (__nv_bfloat16*)out, n);
     return status();
+}
+
+namespace {
+__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ w, __nv_bfloat16* __restrict__ wt, int rows,
+                                 int cols) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)rows * cols) return;
+    const int r = (int)(i / cols), c = (int)(i - (long long)r * cols);
+    wt[(long long)c * rows + r] = w[i];
+}
+}  // namespace
+
+extern "C" int clb_nop_transpose(const void* w, void* wt, int32_t rows, int32_t cols, void* stream) {
+    if (!w || !wt || rows < 1 || cols < 1) return CLB_NOP_ERR_ARG;
+    k_transpose_bf16<<<nblk((long long)rows * cols), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)w,
+                                                                                   (__nv_bfloat16*)wt, rows, cols);
+    return status();
+}
+
+extern "C" int clb_nop_check(void* stream) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return CLB_NOP_ERR_CUDA;
+    unsigned int flag = 0, zero = 0;
+    if (cudaMemcpyFromSymbol(&flag, g_nop_timeout, sizeof(flag)) != cudaSuccess) return CLB_NOP_ERR_CUDA;
+    if (flag && cudaMemcpyToSymbol(g_nop_timeout, &zero, sizeof(zero)) != cudaSuccess) return CLB_NOP_ERR_CUDA;
+    return flag ? CLB_NOP_ERR_TIMEOUT : CLB_NOP_OK;
 }

@@ -12,7 +12,7 @@ with FP32 accumulation, pooling, upsampling, concatenation, loss and Adam.
 PyTorch only provides device memory and the stream.
 
 Network (NHWC, BF16 activations, ReLU after every 3x3 convolution):
-  enc1 128^2: 7 -> 24 -> 24        enc2 64^2: 24 -> 48 -> 48
+  enc1 128^2: 8 -> 24 -> 24        enc2 64^2: 24 -> 48 -> 48
   enc3 32^2: 48 -> 96 -> 96        bottom 16^2: 96 -> 192 -> 192
   dec3 32^2: [up 192 | 96] -> 96 -> 96
   dec2 64^2: [up 96 | 48] -> 48 -> 48
@@ -32,7 +32,7 @@ U_C = 0.1 / math.sqrt(3.0)     # characteristic velocity Ma c_s of Eq. 46, latti
 # Boussinesq pressure variation across the cavity ~ g beta dT L = u_c^2, i.e.
 # a density variation of ~3 u_c^2 = 0.01.
 RHO_SCALE = 0.01
-N_IN, N_OUT = 7, 4
+N_IN, N_OUT = 8, 4
 
 _VP = ctypes.c_void_p
 
@@ -41,7 +41,7 @@ def _lib():
     L = clb.load()
     if not getattr(L, "_nop_ready", False):
         i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
-        L.clb_nop_conv_fwd.argtypes = [_VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, i32, _VP]
+        L.clb_nop_conv_fwd.argtypes = [_VP, _VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_conv_dgrad.argtypes = [_VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_conv_wgrad.argtypes = [_VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_bias_grad.argtypes = [_VP, _VP, i64, i32, _VP]
@@ -52,6 +52,8 @@ def _lib():
         L.clb_nop_adam.argtypes = [_VP, _VP, _VP, _VP, _VP, i64, f32, f32, f32, f32, i32, _VP]
         L.clb_nop_cast_bf16.argtypes = [_VP, _VP, i64, _VP]
         L.clb_nop_zero.argtypes = [_VP, i64, _VP]
+        L.clb_nop_transpose.argtypes = [_VP, _VP, i32, i32, _VP]
+        L.clb_nop_check.argtypes = [_VP]
         L.clb_nop_add_mask.argtypes = [_VP, _VP, _VP, _VP, i64, _VP]
         L._nop_ready = True
     return L
@@ -68,11 +70,13 @@ def _p(t):
 
 # ------------------------------------------------------------------ features
 def features(phi: np.ndarray, Ra: float, Da: float, Pr: float, sigma: float) -> np.ndarray:
-    """(H, W, 7) network input: normalised porosity, log10 Ra, log10 Da, Pr,
-    sigma (broadcast) and the two node coordinates."""
+    """(H, W, 8) network input: normalised porosity, log10 Ra, log10 Da, Pr,
+    sigma (broadcast), the two node coordinates and the mean porosity
+    (broadcast).  Eight channels keep every layer's channel count a
+    multiple of 8, the tensor-core path's granule."""
     phi = np.asarray(phi, dtype=np.float32)
     h, w = phi.shape
-    out = np.empty((h, w, 7), dtype=np.float32)
+    out = np.empty((h, w, N_IN), dtype=np.float32)
     out[..., 0] = (phi - 0.65) / 0.15
     out[..., 1] = (math.log10(Ra) - 4.5) / 0.87
     out[..., 2] = (math.log10(Da) + 2.5) / 0.87
@@ -80,6 +84,7 @@ def features(phi: np.ndarray, Ra: float, Da: float, Pr: float, sigma: float) -> 
     out[..., 4] = (sigma - 1.25) / 0.43
     out[..., 5] = np.linspace(-0.5, 0.5, w, dtype=np.float32)[None, :]
     out[..., 6] = np.linspace(-0.5, 0.5, h, dtype=np.float32)[:, None]
+    out[..., 7] = (float(phi.mean()) - 0.65) / 0.15
     return out
 
 
@@ -164,7 +169,13 @@ class Conv:
         self.gb = torch.zeros_like(self.b)
         self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
         self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
+        self.wbt = torch.empty((cout, taps * cin), dtype=torch.bfloat16, device=dev)   # for the tcgen05 forward
         _ok(_lib().clb_nop_cast_bf16(_p(self.w), _p(self.wb), self.w.numel(), None), "cast")
+        self.refresh_t()
+
+    def refresh_t(self):
+        """Rebuild the transposed BF16 copy from the BF16 weights."""
+        _ok(_lib().clb_nop_transpose(_p(self.wb), _p(self.wbt), self.taps * self.cin, self.cout, None), "transpose")
 
     @property
     def nparams(self):
@@ -191,12 +202,24 @@ class Net:
     def nparams(self):
         return sum(l.nparams for l in self.layers)
 
+    # resolution divisor of each layer (forward order)
+    RES = (1, 1, 2, 2, 4, 4, 8, 8, 4, 4, 2, 2, 1, 1, 1)
+
+    def train_flops(self, n, h, w):
+        """Tensor-core FLOPs of one training step: forward, input gradient
+        (all layers but the first) and weight gradient of every convolution."""
+        tot = 0
+        for i, (l, d) in enumerate(zip(self.layers, self.RES)):
+            one = 2.0 * n * (h // d) * (w // d) * l.taps * l.cin * l.cout
+            tot += one * (2 if i == 0 else 3)
+        return tot
+
     # ---- building blocks (all on the library's kernels)
     def _conv(self, l, x, n, h, w, out_f32=False):
         t = self.torch
         y = t.empty((n, h, w, l.cout), dtype=t.float32 if out_f32 else t.bfloat16, device="cuda")
-        _ok(_lib().clb_nop_conv_fwd(_p(x), _p(l.wb), _p(l.b), _p(y), int(out_f32), int(l.relu), n, h, w, l.cin,
-                                    l.cout, l.taps, None), "conv_fwd")
+        _ok(_lib().clb_nop_conv_fwd(_p(x), _p(l.wb), _p(l.wbt), _p(l.b), _p(y), int(out_f32), int(l.relu), n, h, w,
+                                    l.cin, l.cout, l.taps, None), "conv_fwd")
         return y
 
     def _pool(self, x, n, h, w, c):
@@ -215,7 +238,7 @@ class Net:
         return y
 
     def forward(self, x, n, h, w):
-        """x: (n, h, w, 7) BF16 device tensor -> (n, h, w, 4) FP32, plus the
+        """x: (n, h, w, 8) BF16 device tensor -> (n, h, w, 4) FP32, plus the
         activations the backward pass needs."""
         L = self.layers
         c1, c2, c3, c4 = L[0].cout, L[2].cout, L[4].cout, L[6].cout
@@ -251,8 +274,7 @@ class Net:
         """Accumulate l's weight and bias gradients; return dx (BF16) masked
         by `mask` > 0 (the ReLU of the layer that produced x) if given."""
         lib, t = _lib(), self.torch
-        _ok(lib.clb_nop_conv_wgrad(_p(x), _p(dy), _p(l.gw), n, h, w, l.cin, l.cout, l.taps,
-                                   max(1, min(64, n * h * w // 4096)), None), "wgrad")
+        _ok(lib.clb_nop_conv_wgrad(_p(x), _p(dy), _p(l.gw), n, h, w, l.cin, l.cout, l.taps, 0, None), "wgrad")
         _ok(lib.clb_nop_bias_grad(_p(dy), _p(l.gb), n * h * w, l.cout, None), "bias_grad")
         if not want_dx:
             return None
@@ -318,6 +340,7 @@ class Net:
                                  None), "adam")
             _ok(lib.clb_nop_adam(_p(l.b), _p(l.gb), _p(l.mb), _p(l.vb), None, l.b.numel(), lr, b1, b2, eps, step,
                                  None), "adam")
+            l.refresh_t()
 
     def loss_and_grad(self, out, target, weights=None):
         """Channel-weighted MSE and its gradient (weights: device FP32, one per
@@ -351,6 +374,7 @@ class Net:
             l.wb.copy_(wb)
             l.w.copy_(wb.float())
             l.b.copy_(t.from_numpy(z[f"b{i}"]).to("cuda"))
+            l.refresh_t()
         return self
 
 
@@ -365,7 +389,7 @@ def to_bf16(torch, arr: np.ndarray):
 def train(net: Net, X: np.ndarray, Y: np.ndarray, epochs: int, batch: int = 16, lr: float = 2e-3,
           Xval=None, Yval=None, log=None, weights=None):
     """Adam on the channel-weighted mean squared error (cosine learning-rate
-    decay); X: (N, H, W, 7), Y: (N, H, W, 4).  Returns the per-epoch
+    decay); X: (N, H, W, 8), Y: (N, H, W, 4).  Returns the per-epoch
     (train, validation) losses."""
     torch = net.torch
     n, h, w, _ = X.shape

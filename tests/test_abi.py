@@ -72,10 +72,10 @@ def test_surrogate_entry_points_declared_and_reject_bad_shapes():
         assert n in names
     lib = surrogate._lib()
     fake = ctypes.c_void_p(16)          # never dereferenced: the calls fail validation first
-    assert lib.clb_nop_conv_fwd(fake, fake, None, fake, 0, 1, 1, 8, 8, 4, 4, 5, None) == -1      # taps 5
-    assert lib.clb_nop_conv_fwd(fake, fake, None, fake, 0, 1, 0, 8, 8, 4, 4, 9, None) == -1      # n = 0
-    assert lib.clb_nop_conv_fwd(None, fake, None, fake, 0, 1, 1, 8, 8, 4, 4, 9, None) == -1      # null x
+    assert lib.clb_nop_conv_fwd(fake, fake, None, None, fake, 0, 1, 1, 8, 8, 4, 4, 5, None) == -1      # taps 5
+    assert lib.clb_nop_conv_fwd(fake, fake, None, None, fake, 0, 1, 0, 8, 8, 4, 4, 9, None) == -1      # n = 0
+    assert lib.clb_nop_conv_fwd(None, fake, None, None, fake, 0, 1, 1, 8, 8, 4, 4, 9, None) == -1      # null x
     # 32-bit index guard: 2^16 x 2^16 pixels x 1 channel x 9 taps
-    assert lib.clb_nop_conv_fwd(fake, fake, None, fake, 0, 1, 1, 65536, 65536, 1, 1, 9, None) == -1
+    assert lib.clb_nop_conv_fwd(fake, fake, None, None, fake, 0, 1, 1, 65536, 65536, 1, 1, 9, None) == -1
     assert lib.clb_nop_pool2(fake, fake, 1, 7, 8, 4, 0, None) == -1                            # odd height
     assert lib.clb_nop_adam(fake, fake, fake, fake, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == -1  # t = 0

@@ -28,7 +28,7 @@ def _bf(shape, seed, scale=1.0):
 
 
 def _p(t):
-    return t.data_ptr()
+    return None if t is None else t.data_ptr()
 
 
 def _ref_conv(x_nhwc, wmat, taps, cin, cout, bias=None):
@@ -46,11 +46,15 @@ def _close(a, b, rel):
     assert err <= rel * scale, (err, scale, err / scale)
 
 
-SHAPES = [  # n, h, w, cin, cout, taps: ragged against the 64 x 64 x 32 tiles
-    (2, 12, 20, 7, 24, 9),
+SHAPES = [  # n, h, w, cin, cout, taps: ragged against the 64 x 64 x 32 (mma.sync) and 128 x N x 64 (tcgen05) tiles
+    (2, 12, 20, 7, 24, 9),         # cin 7: forward on mma.sync; input gradient (cout 24) on tcgen05
     (1, 16, 16, 40, 72, 9),
-    (3, 8, 10, 24, 3, 1),
-    (2, 6, 6, 130, 20, 9),
+    (3, 8, 10, 24, 3, 1),          # 1x1, N = 3 padded to 16 on tcgen05; cout 3: input gradient on mma.sync
+    (2, 6, 6, 130, 20, 9),         # neither channel count a multiple of 8: mma.sync both ways
+    (2, 12, 20, 8, 24, 9),
+    (1, 8, 8, 288, 96, 9),         # input gradient N = 288: two N tiles (256 + 32)
+    (2, 10, 6, 24, 192, 9),
+    (3, 16, 12, 48, 96, 9),
 ]
 
 
@@ -64,12 +68,17 @@ def test_conv_forward(lib, shape, relu):
     if relu:
         ref = ref.clamp_min(0)
     xd, wd, bd = x.cuda(), wm.cuda(), b.cuda()
-    y32 = torch.empty((n, h, w, cout), device="cuda")
-    assert lib.clb_nop_conv_fwd(_p(xd), _p(wd), _p(bd), _p(y32), 1, relu, n, h, w, cin, cout, taps, None) == 0
-    _close(y32.cpu(), ref, 1e-5)
-    y16 = torch.empty((n, h, w, cout), device="cuda", dtype=torch.bfloat16)
-    assert lib.clb_nop_conv_fwd(_p(xd), _p(wd), _p(bd), _p(y16), 0, relu, n, h, w, cin, cout, taps, None) == 0
-    _close(y16.cpu(), ref, 8e-3)
+    wt = wm.t().contiguous().cuda()
+    for wtp in (None, wt):             # mma.sync path, then tcgen05 where the shape allows
+        y32 = torch.empty((n, h, w, cout), device="cuda")
+        assert lib.clb_nop_conv_fwd(_p(xd), _p(wd), _p(wtp), _p(bd), _p(y32), 1, relu, n, h, w, cin, cout, taps,
+                                    None) == 0
+        assert lib.clb_nop_check(None) == 0
+        _close(y32.cpu(), ref, 1e-5)
+        y16 = torch.empty((n, h, w, cout), device="cuda", dtype=torch.bfloat16)
+        assert lib.clb_nop_conv_fwd(_p(xd), _p(wd), _p(wtp), _p(bd), _p(y16), 0, relu, n, h, w, cin, cout, taps,
+                                    None) == 0
+        _close(y16.cpu(), ref, 8e-3)
 
 
 @pytest.mark.parametrize("shape", SHAPES)
@@ -83,6 +92,7 @@ def test_conv_input_gradient(lib, shape):
     dx = torch.empty((n, h, w, cin), device="cuda", dtype=torch.bfloat16)
     xd = x.cuda()
     assert lib.clb_nop_conv_dgrad(_p(dy.cuda()), _p(wm.cuda()), _p(xd), _p(dx), n, h, w, cin, cout, taps, None) == 0
+    assert lib.clb_nop_check(None) == 0
     _close(dx.cpu(), ref, 8e-3)
 
 
@@ -96,6 +106,13 @@ def test_conv_weight_gradient(lib, shape, splitk):
     dw = torch.zeros((taps * cin, cout), device="cuda")
     assert lib.clb_nop_conv_wgrad(_p(x.cuda()), _p(dy.cuda()), _p(dw), n, h, w, cin, cout, taps, splitk, None) == 0
     _close(dw.cpu(), wr.grad, 1e-5)
+
+
+def test_transpose(lib):
+    w = _bf((37, 19), 30)
+    wt = torch.empty((19, 37), device="cuda", dtype=torch.bfloat16)
+    assert lib.clb_nop_transpose(_p(w.cuda()), _p(wt), 37, 19, None) == 0
+    assert torch.equal(wt.cpu(), w.t())
 
 
 def test_bias_grad_pool_up_concat(lib):
@@ -218,7 +235,7 @@ def test_network_forward_backward_matches_autograd(lib):
     assert 1.0e6 < net.nparams < 1.3e6
     n, h, w = 2, 32, 24
     g = torch.Generator().manual_seed(21)
-    x = torch.randn((n, h, w, 7), generator=g).to(torch.bfloat16)
+    x = torch.randn((n, h, w, surrogate.N_IN), generator=g).to(torch.bfloat16)
     y = torch.randn((n, h, w, 4), generator=g) * 0.3
     out, A = net.forward(x.cuda(), n, h, w)
     loss, dout = net.loss_and_grad(out, y.cuda())
@@ -242,7 +259,7 @@ def test_training_reduces_the_loss(lib):
     net = surrogate.Net.create(torch, seed=4)
     rng = np.random.default_rng(5)
     n, h, w = 8, 32, 32
-    X = rng.standard_normal((n, h, w, 7)).astype(np.float32)
+    X = rng.standard_normal((n, h, w, surrogate.N_IN)).astype(np.float32)
     yy, xx = np.mgrid[0:h, 0:w] / h
     Y = np.stack([np.sin(np.pi * xx) * X[:, :1, :1, 1], np.cos(np.pi * yy) * X[:, :1, :1, 2],
                   xx + 0 * X[:, :1, :1, 0], yy * X[:, :1, :1, 3]], axis=-1).astype(np.float32)
