@@ -141,7 +141,10 @@ void clb_bc_cavity(clb_bc* bc, double Th, double Tc);
  *   bc     : boundary specification
  *   stream : cudaStream_t to issue all work on, or NULL
  * The state starts at rest: rho = 1, u = 0, T = T_init.  On failure *h is
- * NULL and clb_last_error(NULL) describes the problem. */
+ * NULL and clb_last_error(NULL) describes the problem.  Parameters and grid
+ * size are validated (CLB_ERR_ARG) before phi is read and before any CUDA
+ * call; the FP16 forms accept grids with 9 * ny * pitch < 2^31, pitch = nx
+ * rounded up to a multiple of 64. */
 int clb_init(clb_handle** h, const clb_params* p, const double* phi, const double* ay_row,
              const clb_bc* bc, void* stream);
 

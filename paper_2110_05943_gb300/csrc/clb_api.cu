@@ -333,6 +333,9 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
     const int wall_x = bc->kind[CLB_W] == CLB_WALL, wall_y = bc->kind[CLB_S] == CLB_WALL;
     if ((wall_x && p->nx < 4) || (wall_y && p->ny < 4))
         return fail(nullptr, CLB_ERR_ARG, "clb_init: a walled direction needs at least 4 nodes");
+    // size limits first: phi is not read for a grid that is rejected
+    if (p->precision != CLB_F64 && (long long)((p->nx + 63) / 64 * 64) * p->ny * 9 > 2147483647LL)
+        return fail(nullptr, CLB_ERR_ARG, "clb_init: grid too large for the FP16 forms' 32-bit offsets (9 * ny * pitch >= 2^31)");
     const long long n = (long long)p->nx * p->ny;
     for (long long i = 0; i < n; ++i)
         if (!(phi[i] > 0.0 && phi[i] <= 1.0))
@@ -425,10 +428,6 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
         for (int i = 1; i < 5; ++i) k.wg[i] = (float)(0.25 * p->varpi * p->T0);
     }
     const Geo& G = h->k64.g;
-    if (half && (long long)G.plane * 9 > 2147483647LL) {
-        fail(h, CLB_ERR_ARG, "clb_init: grid too large for the FP16 forms' 32-bit offsets (9 * ny * pitch >= 2^31)");
-        return bail(CLB_ERR_ARG);
-    }
     pick_launch(h);
 
     const size_t fbytes = (size_t)G.plane * 9 * h->es;

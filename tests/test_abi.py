@@ -63,6 +63,24 @@ def test_init_rejects_bad_arguments_before_touching_the_gpu():
         clb.clb_init(p, np.full(256, 0.5), mixed)
 
 
+def test_fp16_grid_size_limit_checked_before_phi_is_read():
+    """The FP16 forms index with 32-bit offsets: 9 * ny * pitch must stay
+    below 2^31.  The limit is checked on the host before the porosity array
+    is read, so a one-value array stands in for the 16384 x 14564 field."""
+    import ctypes as C
+    import numpy as np
+    from paper_2110_05943_gb300 import clb
+    lib = clb.load()
+    bc = clb.clb_bc_cavity()
+    one = np.full(1, 0.5)
+    h = C.c_void_p()
+    for prec, nx, ny in ((clb.CLB_F16N, 16384, 14564), (clb.CLB_F16S, 16385, 14600)):
+        p = clb.clb_params_default(nx=nx, ny=ny, precision=prec)
+        rc = lib.clb_init(C.byref(h), C.byref(p), one.ctypes.data_as(C.POINTER(C.c_double)), None, C.byref(bc), None)
+        assert rc == clb.CLB_ERR_ARG and not h.value
+        assert b"32-bit" in lib.clb_last_error(None)
+
+
 def test_surrogate_entry_points_declared_and_reject_bad_shapes():
     """The learned warm start's kernels (include/clb_nop.h) are exported and
     validate shapes on the host before any launch."""
