@@ -200,9 +200,14 @@ void clb_destroy(clb_handle* h);
  * precision, shift and forchheimer.  Arrays of per-case inputs are indexed
  * by case; phi[c] points to case c's ny*nx host porosity.  Steps advance
  * every active case; clb_batch_set_active takes a flag per case (retired
- * cases keep their state and stop advancing).  clb_batch_tune times each
- * candidate tile shape for `steps` steps (the cases advance meanwhile) and
- * keeps the fastest; *chosen receives its index.  Other conventions as for
+ * cases keep their state and stop advancing; re-activated, they resume
+ * from that state).  clb_batch_tune times each of the 12 candidate tilings
+ * for `steps` steps (the cases advance meanwhile) and keeps the fastest;
+ * *chosen receives its index, choice = 3 * shape + p: shapes 0-3 are blocks
+ * of 64x2, 32x4, 16x8 and 8x16 threads (each thread one node pair in the
+ * FP16 forms, one node in FP64), p selects 4, 16 or 64 tiles per CTA.
+ * clb_batch_set_tiling fixes a choice without timing.  Results do not
+ * depend on the tiling.  Other conventions as for
  * the single-case entry points.  The paper has no batched form; this is the
  * data-parallel way to run parameter studies such as its Table 1. */
 typedef struct clb_batch clb_batch;
@@ -211,6 +216,7 @@ int clb_batch_init(clb_batch** b, int32_t ncase, const clb_params* p, const doub
 int clb_batch_step(clb_batch* b, int64_t n);
 int clb_batch_set_active(clb_batch* b, const int32_t* active);
 int clb_batch_tune(clb_batch* b, int32_t steps, int32_t* chosen);
+int clb_batch_set_tiling(clb_batch* b, int32_t choice);
 /* Mean Nusselt number of `side` for every case (host array of ncase values). */
 int clb_batch_nusselt(clb_batch* b, int32_t side, double* nu);
 /* Macroscopic fields of case c (host arrays of that case's ny*nx values). */

@@ -98,6 +98,7 @@ def load(build_if_needed: bool = True):
     L.clb_batch_step.argtypes = [_VP, ctypes.c_int64]
     L.clb_batch_set_active.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32)]
     L.clb_batch_tune.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    L.clb_batch_set_tiling.argtypes = [_VP, ctypes.c_int32]
     L.clb_batch_nusselt.argtypes = [_VP, ctypes.c_int32, _DP]
     L.clb_batch_macros.argtypes = [_VP, ctypes.c_int32, _DP, _DP, _DP, _DP]
     L.clb_batch_nodes.argtypes = [_VP]
@@ -352,6 +353,10 @@ def clb_batch_set_active(b, active):
     _bcheck(load().clb_batch_set_active(b, a), b)
 
 
+def clb_batch_set_tiling(b, choice: int):
+    _bcheck(load().clb_batch_set_tiling(b, int(choice)), b)
+
+
 def clb_batch_tune(b, steps: int = 4) -> int:
     ch = ctypes.c_int32(-1)
     _bcheck(load().clb_batch_tune(b, int(steps), ctypes.byref(ch)), b)
@@ -405,6 +410,9 @@ class Batch:
 
     def tune(self, steps: int = 4) -> int:
         return clb_batch_tune(self.handle, steps)
+
+    def set_tiling(self, choice: int):
+        clb_batch_set_tiling(self.handle, choice)
 
     def nusselt(self, side: int = W) -> np.ndarray:
         return clb_batch_nusselt(self.handle, len(self), side)

@@ -10,6 +10,7 @@
 struct clb_batch {
     std::vector<clb_handle*> cases;
     std::vector<int32_t> active;
+    std::vector<int32_t> flip;      // case c's current buffer is (par ^ flip[c]) while it is active
     int prec = CLB_F64;
     int shift = 1, forch = 1;
     cudaStream_t stream = nullptr;
@@ -29,8 +30,10 @@ struct clb_batch {
 
 namespace {
 // Candidate block shapes (threads in x, threads in y), 128 threads each.
-constexpr int kNumShapes = 3;
-constexpr int kShapes[kNumShapes][2] = {{64, 2}, {32, 4}, {16, 8}};
+// Taller blocks reuse the pulled rows y - 1, y, y + 1 in L1 across their
+// warps; wider ones waste less on narrow grids.
+constexpr int kNumShapes = 4;
+constexpr int kShapes[kNumShapes][2] = {{64, 2}, {32, 4}, {16, 8}, {8, 16}};
 constexpr int kPerCta[3] = {4, 16, 64};
 }  // namespace
 
@@ -132,9 +135,28 @@ static cudaGraphExec_t batch_capture(clb_batch* b, int par) {
     return ex;
 }
 
-// Keep every case handle's buffer parity and clock in step with the batch.
+// Keep the active case handles' buffer parity in step with the batch; a
+// retired case keeps the parity (the buffer) its state was left in.
 static void batch_sync_cases(clb_batch* b) {
-    for (size_t c = 0; c < b->cases.size(); ++c) b->cases[c]->par = b->par;
+    for (size_t c = 0; c < b->cases.size(); ++c)
+        if (b->active[c]) b->cases[c]->par = b->par ^ b->flip[c];
+}
+
+// Device copy of case c's flip in the case table.
+static int batch_upload_flip(clb_batch* b, size_t c) {
+    using C64 = CaseT<double, double>;
+    using C16 = CaseT<float, __half>;
+    size_t off, stride;
+    if (b->prec == CLB_F64) {
+        off = offsetof(C64, flip);
+        stride = sizeof(C64);
+    } else {
+        off = offsetof(C16, flip);
+        stride = sizeof(C16);
+    }
+    CKB(b, cudaMemcpyAsync((unsigned char*)b->table + c * stride + off, &b->flip[c], sizeof(int32_t),
+                           cudaMemcpyHostToDevice, b->stream));
+    return CLB_OK;
 }
 
 extern "C" int clb_batch_init(clb_batch** out, int32_t ncase, const clb_params* p, const double* const* phi,
@@ -165,6 +187,7 @@ extern "C" int clb_batch_init(clb_batch** out, int32_t ncase, const clb_params* 
         }
         b->cases.push_back(h);
         b->active.push_back(1);
+        b->flip.push_back(0);
     }
     if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
         bfail(b, CLB_ERR_CUDA, "clb_batch_init: stream creation failed");
@@ -181,6 +204,7 @@ extern "C" int clb_batch_init(clb_batch** out, int32_t ncase, const clb_params* 
             t[c].A = h->aux64();
             t[c].b[0] = h->buf<double>(0);
             t[c].b[1] = h->buf<double>(1);
+            t[c].flip = 0;
         }
         bytes = t.size() * sizeof(t[0]);
         host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + bytes);
@@ -192,6 +216,7 @@ extern "C" int clb_batch_init(clb_batch** out, int32_t ncase, const clb_params* 
             t[c].A = h->aux32();
             t[c].b[0] = h->buf<__half>(0);
             t[c].b[1] = h->buf<__half>(1);
+            t[c].flip = 0;
         }
         bytes = t.size() * sizeof(t[0]);
         host.assign((unsigned char*)t.data(), (unsigned char*)t.data() + bytes);
@@ -237,7 +262,17 @@ extern "C" int clb_batch_step(clb_batch* b, int64_t n) {
 
 extern "C" int clb_batch_set_active(clb_batch* b, const int32_t* active) {
     if (!b || !active) return CLB_ERR_ARG;
-    for (size_t c = 0; c < b->cases.size(); ++c) b->active[c] = active[c] != 0;
+    batch_sync_cases(b);
+    for (size_t c = 0; c < b->cases.size(); ++c) {
+        const int32_t now = active[c] != 0;
+        if (now && !b->active[c]) {
+            // resume from the buffer the case was retired in
+            b->flip[c] = b->cases[c]->par ^ b->par;
+            const int rc = batch_upload_flip(b, c);
+            if (rc != CLB_OK) return rc;
+        }
+        b->active[c] = now;
+    }
     return batch_build_tiles(b);
 }
 
@@ -295,6 +330,15 @@ extern "C" int clb_batch_tune(clb_batch* b, int32_t steps, int32_t* chosen) {
     b->per_cta = best_p;
     batch_sync_cases(b);
     if (chosen) *chosen = best_s * 3 + (best_p == kPerCta[0] ? 0 : best_p == kPerCta[1] ? 1 : 2);
+    return batch_build_tiles(b);
+}
+
+extern "C" int clb_batch_set_tiling(clb_batch* b, int32_t choice) {
+    if (!b) return CLB_ERR_ARG;
+    if (choice < 0 || choice >= kNumShapes * 3)
+        return bfail(b, CLB_ERR_ARG, "clb_batch_set_tiling: choice %d outside [0, %d)", choice, kNumShapes * 3);
+    b->shape = choice / 3;
+    b->per_cta = kPerCta[choice % 3];
     return batch_build_tiles(b);
 }
 

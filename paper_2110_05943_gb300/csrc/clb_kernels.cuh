@@ -960,6 +960,8 @@ struct CaseT {
     KParamsT<R> K;
     AuxT<R> A;
     BufT<S> b[2];
+    int flip;       // the case's current buffer is b[par ^ flip] (par: the batch's parity)
+    int pad_;
 };
 
 // Independent cases advanced by one launch.  `tiles` lists (case, x0, y0)
@@ -991,9 +993,9 @@ __global__ void __launch_bounds__(128, 4) k_step_batch(const CaseT<typename P::R
         const int x = tl.y + NPT * threadIdx.x, y = tl.z + threadIdx.y;
         if (x < sc.K.g.nx && y < sc.K.g.ny) {
             if constexpr (NPT == 2)
-                step_pair<P, SHIFT, FORCH>(sc.b[par], sc.b[1 - par], sc.A, sc.K, x, y);
+                step_pair<P, SHIFT, FORCH>(sc.b[par ^ sc.flip], sc.b[1 - (par ^ sc.flip)], sc.A, sc.K, x, y);
             else
-                step_node<P, SHIFT, FORCH>(sc.b[par], sc.b[1 - par], sc.A, sc.K, x, y);
+                step_node<P, SHIFT, FORCH>(sc.b[par ^ sc.flip], sc.b[1 - (par ^ sc.flip)], sc.A, sc.K, x, y);
         }
     }
 }

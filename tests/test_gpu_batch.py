@@ -86,15 +86,44 @@ def test_retired_cases_freeze_and_tuning_keeps_results(prec):
     active = [1] * n
     active[1] = 0
     batch.set_active(active)
-    choice = batch.tune(steps=2)          # 9 shapes x 3 steps = 27 more steps for the active cases
-    assert 0 <= choice < 9
+    choice = batch.tune(steps=2)          # 12 tilings x 3 steps = 36 more steps for the active cases
+    assert 0 <= choice < 12
     batch.step(33)
     for a, b in zip(batch.macros(1), frozen):
         assert np.array_equal(a, b)
-    total = 40 + 27 + 33
+    total = 40 + 36 + 33
     for c in (0, 2, 4):
         s = _single(params[c], phis[c])
         s.step(total)
+        for a, b in zip(batch.macros(c), s.macros()):
+            assert np.array_equal(a, b), (prec, c)
+        s.close()
+    # 69 batch steps (an odd count) after retirement: the case resumes from its own buffer
+    batch.set_active([1] * n)
+    batch.step(11)
+    s = _single(params[1], phis[1])
+    s.step(40 + 11)
+    for a, b in zip(batch.macros(1), s.macros()):
+        assert np.array_equal(a, b), prec
+    s.close()
+    batch.close()
+
+
+@pytest.mark.parametrize("prec", [0, 2])
+def test_every_tiling_gives_the_same_bits(prec):
+    """Five steps under each of the 12 tilings in turn (four block shapes,
+    4/16/64 tiles per CTA) equal 60 stand-alone steps."""
+    from paper_2110_05943_gb300 import clb
+    spec, params, phis = _cases(prec)
+    batch = clb.Batch(params, phis, [clb.clb_bc_cavity(1.0, 0.0) for _ in params])
+    for choice in range(12):
+        batch.set_tiling(choice)
+        batch.step(5)
+    with pytest.raises(clb.ClbError):
+        batch.set_tiling(12)
+    for c, (p, phi) in enumerate(zip(params, phis)):
+        s = _single(p, phi)
+        s.step(60)
         for a, b in zip(batch.macros(c), s.macros()):
             assert np.array_equal(a, b), (prec, c)
         s.close()
