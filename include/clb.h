@@ -53,12 +53,15 @@ enum { CLB_ADIABATIC = 0, CLB_ISOTHERMAL = 1 };
  *              rest state (w_i rho_0 for f, the D2Q5 equilibrium at u = 0,
  *              T = T0 for g), arithmetic in FP32; 60 B per node update.
  *              The rest population's deviation is O(dT), so T is quantised
- *              at ~2e-4 dT every step: fine for transients, not for
- *              converged Nusselt numbers.
+ *              at ~2e-4 dT every step: steady Nusselt numbers carry
+ *              errors of 1e-4 to a few 1e-2 and visible noise.
  *   CLB_F16N : each post-collision value stored in FP16 as its deviation
  *              from the local equilibrium of the node that wrote it, plus
  *              that node's (rho - 1, u, T - T0) in FP16 as the baseline;
- *              FP32 arithmetic; 76 B per node update. */
+ *              FP32 arithmetic; 76 B per node update.
+ * Both FP16 forms store the deviations times 2^12 with unbiased stochastic
+ * rounding, seeded by the node and a per-buffer step counter (runs are
+ * deterministic, and checkpoints carry the counter). */
 enum { CLB_F64 = 0, CLB_F16S = 1, CLB_F16N = 2 };
 
 /* Boundary specification.  Opposite sides must both be periodic or both

@@ -51,6 +51,7 @@ struct clb_handle {
     void* f[2] = {nullptr, nullptr};
     void* g[2] = {nullptr, nullptr};
     uint2* rec[2] = {nullptr, nullptr};   // FP16N form: per-node baseline record
+    unsigned* seq = nullptr;              // FP16 forms: step counter of each buffer (seeds the rounding)
     int par = 0;
     CoefT<double>* coef = nullptr;   // FP64 form: per-node constants
     float* phi32 = nullptr;          // FP16 forms: porosity (dense) or 1/phi (pitched)
@@ -74,7 +75,7 @@ struct clb_handle {
                                 : AuxT<float>{nullptr, phi32, nullptr, (const float*)ayg};
     }
     template <typename S>
-    BufT<S> buf(int i) const { return BufT<S>{(S*)f[i], (S*)g[i], rec[i]}; }
+    BufT<S> buf(int i) const { return BufT<S>{(S*)f[i], (S*)g[i], rec[i], seq ? seq + i : nullptr}; }
     const Geo& geo() const { return k64.g; }
     // bytes per node of one stored state (distributions + record)
     size_t node_bytes() const { return 14 * es + (prec == CLB_F16N ? sizeof(uint2) : 0); }
@@ -221,6 +222,7 @@ static void free_all(clb_handle* h) {
         cudaFree(h->g[i]);
         cudaFree(h->rec[i]);
     }
+    cudaFree(h->seq);
     cudaFree(h->coef);
     cudaFree(h->phi32);
     cudaFree(h->ayg);
@@ -435,6 +437,10 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
 
     const size_t fbytes = (size_t)G.plane * 9 * h->es;
     const size_t gbytes = (size_t)G.plane * 5 * h->es;
+    if (half) {
+        CKI(cudaMalloc(&h->seq, 2 * sizeof(unsigned)));
+        CKI(cudaMemsetAsync(h->seq, 0, 2 * sizeof(unsigned), h->stream));
+    }
     for (int i = 0; i < 2; ++i) {
         CKI(cudaMalloc(&h->f[i], fbytes));
         CKI(cudaMalloc(&h->g[i], gbytes));
@@ -632,8 +638,9 @@ extern "C" int clb_lattice_params(const clb_handle* h, clb_lattice* out) {
 }
 
 // Checkpoint layout: 8 int64 header words (magic, version, nx, ny,
-// precision, t, 0, 0), then f (9 planes) and g (5 planes), each plane ny*nx
-// stored values (FP64, or the FP16 deviations) without pitch padding.
+// precision, t, step counter of the FP16 forms, 0), then f (9 planes) and
+// g (5 planes), each plane ny*nx stored values (FP64, or the FP16
+// deviations) without pitch padding.
 static const int64_t kMagic = 0x434c42314750554cLL;
 
 extern "C" size_t clb_state_bytes(const clb_handle* h) {
@@ -666,7 +673,12 @@ static int copy_state(clb_handle* h, int b, char* host, bool to_host) {
 extern "C" int clb_get_state(clb_handle* h, void* buf, size_t bytes) {
     if (!h || !buf) return CLB_ERR_ARG;
     if (bytes < clb_state_bytes(h)) return fail(h, CLB_ERR_ARG, "clb_get_state: buffer too small");
-    int64_t hdr[8] = {kMagic, 1, h->prm.nx, h->prm.ny, h->prm.precision, h->t, 0, 0};
+    unsigned seq = 0;
+    if (h->seq) {
+        CK(h, cudaMemcpyAsync(&seq, h->seq + h->par, sizeof seq, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    int64_t hdr[8] = {kMagic, 1, h->prm.nx, h->prm.ny, h->prm.precision, h->t, (int64_t)seq, 0};
     std::memcpy(buf, hdr, sizeof hdr);
     return copy_state(h, h->par, (char*)buf + sizeof hdr, true);
 }
@@ -680,7 +692,11 @@ extern "C" int clb_set_state(clb_handle* h, const void* buf, size_t bytes) {
         hdr[4] != h->prm.precision)
         return fail(h, CLB_ERR_STATE, "clb_set_state: checkpoint does not match this simulation");
     h->par = 0;
-    const int rc = copy_state(h, 0, (char*)buf + sizeof hdr, false);
+    if (h->seq) {
+        const unsigned seq = (unsigned)hdr[6];
+        CK(h, cudaMemcpyAsync(h->seq, &seq, sizeof seq, cudaMemcpyHostToDevice, h->stream));
+    }
+    const int rc = copy_state(h, 0, (char*)buf + sizeof hdr, false);   // synchronises the stream
     if (rc != CLB_OK) return rc;
     h->t = hdr[5];
     return CLB_OK;

@@ -114,12 +114,59 @@ struct BufT {
     S* f;
     S* g;
     uint2* rec;
+    unsigned* seq;   // FP16 forms: steps taken to reach the state this buffer holds (seeds the rounding)
 };
 
 template <typename S>
 __host__ __device__ inline BufT<const S> as_const(const BufT<S>& b) {
-    return BufT<const S>{b.f, b.g, b.rec};
+    return BufT<const S>{b.f, b.g, b.rec, b.seq};
 }
+
+// ---------------------------------------------------------------- rounding
+// The FP16 forms store their values with unbiased stochastic rounding:
+// round-to-nearest of a value that depends on the state is a systematic
+// error that the time march accumulates (it acts as a steady heat source),
+// whereas randomised rounding leaves zero-mean noise.  Six random bits per
+// value are added below the 10 kept mantissa bits (13 bits are discarded
+// between FP32 and FP16) together with half of the remaining 2^7, then the
+// value is truncated towards zero; the expected stored value equals the FP32
+// value to 1/128 of an FP16 unit in the last place (in FP16's normal range).
+// The bits come from the 32-bit integer mixer "lowbias32" (C. Wellons'
+// hash-prospector) keyed by the node's plane offset and the buffer's step
+// counter, so runs stay deterministic and bit-reproducible.
+CLB_HD uint32_t mix32(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+struct Dither {
+    uint32_t h[3];   // 15 six-bit fields: values 0-8 (f), 9-13 (g)
+};
+
+CLB_HD Dither dither_for(uint32_t node, uint32_t seq) {
+    Dither d;
+    d.h[0] = mix32(node * 0x9E3779B1U ^ mix32(seq + 0x632BE5ABU));
+    d.h[1] = mix32(d.h[0] + 0x85EBCA77U);
+    d.h[2] = mix32(d.h[1] + 0xC2B2AE3DU);
+    return d;
+}
+
+CLB_HD uint32_t dbits(const Dither& d, int i) { return (d.h[i / 5] >> (6 * (i % 5))) & 63U; }
+
+CLB_HD __half sr_half(float v, uint32_t r6) {
+    return __float2half_rz(__uint_as_float(__float_as_uint(v) + ((r6 << 7) | 0x40U)));
+}
+
+// Stored FP16 values are the deviations times 2^12 (exact): most
+// deviations of the equilibrium-shifted form lie below FP16's smallest
+// normal number (6.1e-5), where FP16 has a fixed spacing and the dithered
+// rounding above would truncate; scaled, everything above 1.5e-8 is normal.
+// The largest storable deviation is 16.
+constexpr float kDevScale = 4096.0f, kDevInv = 1.0f / 4096.0f;
 
 __device__ __forceinline__ int wrap_lo(int a, int n) { return a < 0 ? a + n : a; }
 __device__ __forceinline__ int wrap_hi(int a, int n) { return a >= n ? a - n : a; }
@@ -483,7 +530,7 @@ struct StoreF64 {
         pull5(B, A, K, x, y, g);
     }
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
-                                                 const R (&f)[9], const R (&g)[5], R, R, R, R, R) {
+                                                 const R (&f)[9], const R (&g)[5], R, R, R, R, R, uint32_t) {
         const long long o = (long long)y * K.g.px + x;
 #pragma unroll
         for (int i = 0; i < 9; ++i) B.f[i * K.g.plane + o] = f[i];
@@ -517,7 +564,7 @@ struct StoreH16 {
         sources<int>(K.g, x, y, o);
         const int Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = K.wf[i] + __half2float(__ldg(B.f + i * Q + o[i]));
+        for (int i = 0; i < 9; ++i) f[i] = fma(__half2float(__ldg(B.f + i * Q + o[i])), kDevInv, K.wf[i]);
     }
     static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
                                                  int y, R (&g)[5]) {
@@ -525,7 +572,7 @@ struct StoreH16 {
         sources<int>(K.g, x, y, o);
         const int Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = K.wg[i] + __half2float(__ldg(B.g + i * Q + o[i]));
+        for (int i = 0; i < 5; ++i) g[i] = fma(__half2float(__ldg(B.g + i * Q + o[i])), kDevInv, K.wg[i]);
     }
     static __device__ __forceinline__ void pull(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
                                                 int y, R (&f)[9], R (&g)[5]) {
@@ -533,12 +580,13 @@ struct StoreH16 {
         pull5(B, A, K, x, y, g);
     }
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
-                                                 const R (&f)[9], const R (&g)[5], R, R, R, R, R) {
+                                                 const R (&f)[9], const R (&g)[5], R, R, R, R, R, uint32_t seq) {
         const int o = y * K.g.px + x, Q = (int)K.g.plane;
+        const Dither d = dither_for((uint32_t)o, seq);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = __float2half_rn(f[i] - K.wf[i]);
+        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - K.wf[i]) * kDevScale, dbits(d, i));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = __float2half_rn(g[i] - K.wg[i]);
+        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half((g[i] - K.wg[i]) * kDevScale, dbits(d, 9 + i));
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
@@ -557,28 +605,32 @@ struct StoreH16 {
             float2 v;
             if (column_dir(i)) v = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.f + i * Q + o0[i])));
             else v = make_float2(__half2float(__ldg(B.f + i * Q + o0[i])), __half2float(__ldg(B.f + i * Q + o1[i])));
-            f[i] = f2(K.wf[i]) + f2::make(v.x, v.y);
+            f[i] = fma(f2::make(v.x, v.y), f2(kDevInv), f2(K.wf[i]));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             float2 v;
             if (column_dir(i)) v = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.g + i * Q + o0[i])));
             else v = make_float2(__half2float(__ldg(B.g + i * Q + o0[i])), __half2float(__ldg(B.g + i * Q + o1[i])));
-            g[i] = f2(K.wg[i]) + f2::make(v.x, v.y);
+            g[i] = fma(f2::make(v.x, v.y), f2(kDevInv), f2(K.wg[i]));
         }
     }
     static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
-                                                  const f2 (&f)[9], const f2 (&g)[5], f2, f2, f2, f2, f2) {
+                                                  const f2 (&f)[9], const f2 (&g)[5], f2, f2, f2, f2, f2,
+                                                  uint32_t seq) {
         const int o = y * K.g.px + x0, Q = (int)K.g.plane;
+        const Dither d0 = dither_for((uint32_t)o, seq), d1 = dither_for((uint32_t)o + 1U, seq);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const f2 d = f[i] - f2(K.wf[i]);
-            *reinterpret_cast<__half2*>(B.f + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+            const f2 d = (f[i] - f2(K.wf[i])) * f2(kDevScale);
+            *reinterpret_cast<__half2*>(B.f + i * Q + o) =
+                __halves2half2(sr_half(d.lo(), dbits(d0, i)), sr_half(d.hi(), dbits(d1, i)));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            const f2 d = g[i] - f2(K.wg[i]);
-            *reinterpret_cast<__half2*>(B.g + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+            const f2 d = (g[i] - f2(K.wg[i])) * f2(kDevScale);
+            *reinterpret_cast<__half2*>(B.g + i * Q + o) =
+                __halves2half2(sr_half(d.lo(), dbits(d0, 9 + i)), sr_half(d.hi(), dbits(d1, 9 + i)));
         }
     }
 };
@@ -640,10 +692,10 @@ __device__ __forceinline__ void pull_one(const BufT<const __half>& B, const AuxT
                                          const int (&o)[9], float (&f)[9], float (&g)[5], bool want_f, bool want_g) {
     const Base s = load_base(B, A, K, o[I]);
     const int Q = (int)K.g.plane;
-    if (want_f) f[I] = feq_comp<I>(s.rho, s.X, s.Y, s.ip) + __half2float(__ldg(B.f + I * Q + o[I]));
+    if (want_f) f[I] = fma(__half2float(__ldg(B.f + I * Q + o[I])), kDevInv, feq_comp<I>(s.rho, s.X, s.Y, s.ip));
     if (I < 5 && want_g)
-        g[I < 5 ? I : 0] = geq_comp<(I < 5 ? I : 0)>(s.T, s.X, s.Y, K.p.sigma, K.p.cT2) +
-                           __half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o[I]));
+        g[I < 5 ? I : 0] = fma(__half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o[I])), kDevInv,
+                               geq_comp<(I < 5 ? I : 0)>(s.T, s.X, s.Y, K.p.sigma, K.p.cT2));
 }
 
 struct StoreH16N {
@@ -680,7 +732,8 @@ struct StoreH16N {
     // The record is rounded first and the baseline rebuilt from the rounded
     // halves, exactly as a reader will rebuild it.
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
-                                                 const R (&f)[9], const R (&g)[5], R rho, R X, R Y, R T, R ip) {
+                                                 const R (&f)[9], const R (&g)[5], R rho, R X, R Y, R T, R ip,
+                                                 uint32_t seq) {
         const int o = y * K.g.px + x, Q = (int)K.g.plane;
         const __half2 a = __floats2half2_rn(rho - 1.0f, X);
         const __half2 b = __floats2half2_rn(Y, T - K.T0);
@@ -698,10 +751,11 @@ struct StoreH16N {
         const float ge[5] = {geq_comp<0>(bT, bX, bY, s, c), geq_comp<1>(bT, bX, bY, s, c),
                              geq_comp<2>(bT, bX, bY, s, c), geq_comp<3>(bT, bX, bY, s, c),
                              geq_comp<4>(bT, bX, bY, s, c)};
+        const Dither d = dither_for((uint32_t)o, seq);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = __float2half_rn(f[i] - fe[i]);
+        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - fe[i]) * kDevScale, dbits(d, i));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = __float2half_rn(g[i] - ge[i]);
+        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half((g[i] - ge[i]) * kDevScale, dbits(d, 9 + i));
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
@@ -737,10 +791,11 @@ struct StoreH16N {
         const float2 b1 = __half22float2(*reinterpret_cast<const __half2*>(&r1.y));
         const f2 rho = f2(1.0) + f2::make(a0.x, a1.x), X = f2::make(a0.y, a1.y), Y = f2::make(b0.x, b1.x);
         const f2 ipp = f2::make(ip.x, ip.y);
-        f[I] = feq_comp<I>(rho, X, Y, ipp) + f2::make(df.x, df.y);
+        f[I] = fma(f2::make(df.x, df.y), f2(kDevInv), feq_comp<I>(rho, X, Y, ipp));
         if (I < 5) {
             const f2 T = f2(K.T0) + f2::make(b0.y, b1.y);
-            g[I < 5 ? I : 0] = geq_comp<(I < 5 ? I : 0)>(T, X, Y, f2(K.p.sigma), f2(K.p.cT2)) + f2::make(dg.x, dg.y);
+            g[I < 5 ? I : 0] =
+                fma(f2::make(dg.x, dg.y), f2(kDevInv), geq_comp<(I < 5 ? I : 0)>(T, X, Y, f2(K.p.sigma), f2(K.p.cT2)));
         }
     }
     static __device__ __forceinline__ void pull2(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x0,
@@ -759,7 +814,8 @@ struct StoreH16N {
         pull2_one<8>(B, A, K, o0, o1, f, g);
     }
     static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
-                                                  const f2 (&f)[9], const f2 (&g)[5], f2 rho, f2 X, f2 Y, f2 T, f2 ip) {
+                                                  const f2 (&f)[9], const f2 (&g)[5], f2 rho, f2 X, f2 Y, f2 T, f2 ip,
+                                                  uint32_t seq) {
         const int o = y * K.g.px + x0, Q = (int)K.g.plane;
         const __half2 a0 = __floats2half2_rn(rho.lo() - 1.0f, X.lo()), b0 = __floats2half2_rn(Y.lo(), T.lo() - K.T0);
         const __half2 a1 = __floats2half2_rn(rho.hi() - 1.0f, X.hi()), b1 = __floats2half2_rn(Y.hi(), T.hi() - K.T0);
@@ -779,15 +835,18 @@ struct StoreH16N {
         const f2 s = f2(K.p.sigma), c = f2(K.p.cT2);
         const f2 ge[5] = {geq_comp<0>(bT, bX, bY, s, c), geq_comp<1>(bT, bX, bY, s, c), geq_comp<2>(bT, bX, bY, s, c),
                           geq_comp<3>(bT, bX, bY, s, c), geq_comp<4>(bT, bX, bY, s, c)};
+        const Dither d0 = dither_for((uint32_t)o, seq), d1 = dither_for((uint32_t)o + 1U, seq);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const f2 d = f[i] - fe[i];
-            *reinterpret_cast<__half2*>(B.f + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+            const f2 d = (f[i] - fe[i]) * f2(kDevScale);
+            *reinterpret_cast<__half2*>(B.f + i * Q + o) =
+                __halves2half2(sr_half(d.lo(), dbits(d0, i)), sr_half(d.hi(), dbits(d1, i)));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            const f2 d = g[i] - ge[i];
-            *reinterpret_cast<__half2*>(B.g + i * Q + o) = __floats2half2_rn(d.lo(), d.hi());
+            const f2 d = (g[i] - ge[i]) * f2(kDevScale);
+            *reinterpret_cast<__half2*>(B.g + i * Q + o) =
+                __halves2half2(sr_half(d.lo(), dbits(d0, 9 + i)), sr_half(d.hi(), dbits(d1, 9 + i)));
         }
     }
 };
@@ -891,6 +950,17 @@ __device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin,
 }
 
 // ---------------------------------------------------------------- kernels
+// Step counter of the input buffer (FP16 forms; 0 without one); the thread
+// of node (0, 0) writes the next value into the output buffer, which no
+// thread of this launch reads.
+template <typename S>
+__device__ __forceinline__ uint32_t step_seq(const BufT<S>& in, const BufT<S>& out, int x, int y) {
+    if (!in.seq) return 0U;
+    const uint32_t seq = *in.seq;
+    if (x == 0 && y == 0) *out.seq = seq + 1U;
+    return seq;
+}
+
 // One node's complete step: pull (or wall rebuild), macros, both collisions, store.
 template <class P, bool SHIFT, bool FORCH>
 __device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
@@ -901,10 +971,11 @@ __device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const B
     R f[9], g[5];
     R rho, X, Y, T, Fx, Fy, n0;
     Mom9T<R> k;
+    const uint32_t seq = step_seq(in, out, x, y);
     node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Fx, Fy, n0);
     collide9<R, SHIFT>(f, k, rho, X, Y, Fx, Fy, c.ip, K.p);
     collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
-    P::store(out, K, x, y, f, g, rho, X, Y, T, c.ip);
+    P::store(out, K, x, y, f, g, rho, X, Y, T, c.ip, seq);
 }
 
 template <class P, bool SHIFT, bool FORCH>
@@ -941,7 +1012,7 @@ __device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const B
     macro_velocity<f2, FORCH>(k.rho, k.jx, k.jy, T, f2(A.ayg[y]), c, P2, X, Y, Fx, Fy);
     collide9<f2, SHIFT>(f, k, k.rho, X, Y, Fx, Fy, c.ip, P2);
     collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
-    P::store2(out, K, x0, y, f, g, k.rho, X, Y, T, c.ip);
+    P::store2(out, K, x0, y, f, g, k.rho, X, Y, T, c.ip, step_seq(in, out, x0, y));
 }
 
 template <class P, bool SHIFT, bool FORCH>
@@ -1054,7 +1125,8 @@ __global__ void k_set_fields(const BufT<typename P::S> out, const AuxT<typename 
         }
     }
     const long long n = (long long)y * K.g.nx + x;
-    P::store(out, K, x, y, f, g, (R)rho[n], (R)ux[n], (R)uy[n], (R)T[n], P::template coef<false>(A, K, x, y).ip);
+    P::store(out, K, x, y, f, g, (R)rho[n], (R)ux[n], (R)uy[n], (R)T[n], P::template coef<false>(A, K, x, y).ip,
+             out.seq ? *out.seq : 0U);
 }
 
 // Four consecutive dense fields of n values set to constants.
