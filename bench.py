@@ -177,12 +177,16 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def steady_state_forms(clb, torch):
+def steady_state_forms(clb, torch, total=350_000, window=20, every=2500):
     """Time to steady state of each storage form on the paper's own grid for
     the Table 1 row Da 1e-2, Ra 1e4, phi 0.6, Pr 1 (128^2; paper: Nu 1.4873):
     steps and wall time until the hot-wall Nusselt number changes by at most
-    1e-4 (relative) over 1000 steps, the Nusselt number then, and its
-    difference from the FP64 form's."""
+    1e-4 (relative) over 1000 steps, and the Nusselt number then.  Each run
+    then continues to `total` steps; the mean Nusselt number over the last
+    window x every steps is the converged value that the forms are compared
+    by (at the stopping step they are still in the slow tail of the
+    transient, so their difference there says little about storage
+    precision)."""
     out = {}
     for name, prec in (("f64", 0), ("f16n", 2), ("f16s", 1)):
         p = clb.clb_params_default(nx=128, ny=128, Ra=1e4, Da=1e-2, Pr=1.0, precision=prec)
@@ -199,17 +203,26 @@ def steady_state_forms(clb, torch):
                 done = (sim.time, time.perf_counter() - t0, nu)
                 break
             prev = nu
+        sim.step(max(0, total - window * every - sim.time))
+        vals = []
+        for _ in range(window):
+            sim.step(every)
+            vals.append(sim.nusselt(clb.W))
         sim.close()
         out[name] = {"steps": done[0] if done else None, "seconds": done[1] if done else None,
-                     "nu": done[2] if done else None}
+                     "nu": done[2] if done else None, "nu_converged": float(np.mean(vals)),
+                     "nu_converged_sd": float(np.std(vals))}
     ref = out["f64"]
     for name in ("f16n", "f16s"):
         o = out[name]
+        o["rel_nu_converged_vs_f64"] = abs(o["nu_converged"] / ref["nu_converged"] - 1)
         if o["nu"] is not None and ref["nu"] is not None:
             o["rel_nu_vs_f64"] = abs(o["nu"] / ref["nu"] - 1)
             o["speedup_vs_f64"] = ref["seconds"] / o["seconds"]
     return {"workload": "128x128 cavity, phi 0.6, Da 1e-2, Ra 1e4, Pr 1 (Table 1 row; paper Nu 1.4873)",
-            "criterion": "|dNu| <= 1e-4 Nu over 1000 steps", "forms": out}
+            "criterion": "|dNu| <= 1e-4 Nu over 1000 steps (time to steady); converged Nu = mean over steps "
+                         f"{total - window * every}..{total}",
+            "forms": out}
 
 
 FORMS = {  # storage form -> (precision code, algorithmic bytes per coupled cell update)
