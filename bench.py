@@ -229,6 +229,12 @@ FORMS = {  # storage form -> (precision code, algorithmic bytes per coupled cell
     "f16n": (2, 28 * 2 + 2 * 8 + 4),   # 14 FP16 deviations read+written, 8 B record read+written, FP32 1/phi
     "f16s": (1, 28 * 2 + 4),           # 14 FP16 deviations read+written, FP32 phi
 }
+# DRAM bytes (read + write) per node of one k_step2 launch, ncu on the 4096^2
+# case (profiles/k_step2_*_cavity4096.md); traffic grows with the node count.
+FORMS_DRAM_PER_NODE = {"f16n": 73.8, "f16s": 57.9}
+# DRAM bytes (read + write) of one k_step_batch launch on the 512-case workload
+# (45.0 M nodes, 8 x 16 blocks): 80.7 B/node, ncu (profiles/k_step_batch_cases512.md).
+BATCH_DRAM_PER_LAUNCH = 3.631e9
 
 
 def reduced_precision_forms(clb, torch, args, hbm_peak, src):
@@ -257,8 +263,10 @@ def reduced_precision_forms(clb, torch, args, hbm_peak, src):
                      "value": n * n * steps / t / 1e6, "unit": UNIT, "steps": steps, "ms_per_step": t / steps * 1e3,
                      "dtype": "f32 arithmetic, f16 storage",
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
-                                  "frac": gbs / hbm_peak, "bytes_per_ccu": bpn, "traffic": None,
-                                  "kernel": f"k_step<StoreH16{'N' if name == 'f16n' else ''}>",
+                                  "frac": gbs / hbm_peak, "bytes_per_ccu": bpn,
+                                  "traffic": FORMS_DRAM_PER_NODE[name] * n * n,
+                                  "traffic_source": "ncu dram bytes per node at 4096^2 x nodes per launch",
+                                  "kernel": f"k_step2<StoreH16{'N' if name == 'f16n' else ''}>",
                                   "peak_source": f"{src} hbm_gbs"}}
     return out
 
@@ -267,10 +275,10 @@ def batched_form(clb, torch, args, hbm_peak, src):
     """512 seeded cavities of uneven size (sides log-uniform in [64, 1024],
     aspect 1-4; log10 Ra in [3, 6], log10 Da in [-4, -1], eps in [0.4, 0.9],
     sigma in [0.5, 2], Pr 0.71) advanced by one FP16N launch per step with
-    the tile shape chosen by clb_batch_tune; aggregate MLUPS over the timed
-    steps.  Accuracy: the 8 cases with the shortest diffusion time run until their Nusselt numbers
-    change by less than 1e-6 (FP64) / 1e-5 (FP16N) relative per 4000 steps,
-    at most 240,000 steps, in FP16N and in FP64; relative difference per case."""
+    the tiling chosen by clb_batch_tune; aggregate MLUPS over the timed
+    steps.  Accuracy: the 8 cases with the shortest diffusion time, as a
+    batch in FP64 and in FP16N, converged (criteria below); relative
+    difference of the hot-wall Nusselt number per case."""
     from paper_2110_05943_gb300.inputs import batch_cases
     cases = batch_cases(512, seed=7)
     stream = torch.cuda.current_stream()
@@ -305,31 +313,54 @@ def batched_form(clb, torch, args, hbm_peak, src):
         return max(c.nx, c.ny) ** 2 / (nu / c.Pr)
     quick = sorted(range(len(cases)), key=lambda i: t_diff(cases[i]))[:8]
     sel = [cases[i] for i in quick]
-    res = {}
-    for prec, tol in ((0, 1e-6), (2, 1e-5)):
-        v = make(sel, prec)
-        prev = v.nusselt(0)
-        t0 = time.perf_counter()
-        while v.time < 240_000:
-            v.step(4000)
-            cur = v.nusselt(0)
-            if np.all(np.abs(cur - prev) <= tol * np.abs(cur)):
-                break
-            prev = cur
-        res[prec] = (cur, v.time, time.perf_counter() - t0)
-        v.close()
-    err = np.abs(res[2][0] / res[0][0] - 1)
+    # FP64: to |dNu| <= 1e-6 Nu per 4000 steps.  FP16N: its time to steady by
+    # the metric's |dNu| <= 1e-4 Nu per 1000 steps (its stochastic rounding
+    # leaves Nu fluctuations of ~1e-5, so a tighter rule never fires), then
+    # on to the FP64 run's step count plus 40,000 and the mean Nu over the
+    # last 20,000 steps; errors are taken between those converged values.
+    v = make(sel, 0)
+    prev = v.nusselt(0)
+    t0 = time.perf_counter()
+    while v.time < 240_000:
+        v.step(4000)
+        nu64 = v.nusselt(0)
+        if np.all(np.abs(nu64 - prev) <= 1e-6 * np.abs(nu64)):
+            break
+        prev = nu64
+    steps64, sec64 = v.time, time.perf_counter() - t0
+    v.close()
+    v = make(sel, 2)
+    prev = v.nusselt(0)
+    t0 = time.perf_counter()
+    while v.time < 240_000:
+        v.step(1000)
+        cur = v.nusselt(0)
+        if np.all(np.abs(cur - prev) <= 1e-4 * np.abs(cur)):
+            break
+        prev = cur
+    steps16, sec16 = v.time, time.perf_counter() - t0
+    v.step(max(0, steps64 + 20_000 - v.time))
+    vals = []
+    for _ in range(20):
+        v.step(1000)
+        vals.append(v.nusselt(0))
+    nu16 = np.mean(vals, axis=0)
+    v.close()
+    err = np.abs(nu16 / nu64 - 1)
     return {"workload": "512 seeded porous cavities (batch_cases seed 7), uneven grids, FP16N",
             "value": nodes * steps / t / 1e6, "unit": UNIT, "steps": steps, "nodes_per_step": nodes,
             "ms_per_step": t / steps * 1e3, "tile_choice": choice, "finite_cases": int(np.isfinite(nu).sum()),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                         "bytes_per_ccu": bpn, "traffic": None, "kernel": "k_step_batch<StoreH16N>",
-                         "peak_source": f"{src} hbm_gbs"},
+                         "bytes_per_ccu": bpn, "traffic": BATCH_DRAM_PER_LAUNCH,
+                         "traffic_source": "ncu dram bytes of one launch of this workload (tiling 9)",
+                         "kernel": "k_step_batch<StoreH16N>", "peak_source": f"{src} hbm_gbs"},
             "validation": {"cases": [f"{c.nx}x{c.ny} Ra {c.Ra:.3g} Da {c.Da:.3g} eps {c.phi:.2f} sigma {c.sigma:.2f}"
                                      for c in sel],
-                           "nu_f64": [float(x) for x in res[0][0]], "nu_f16n": [float(x) for x in res[2][0]],
-                           "max_rel_nu_error": float(np.nanmax(err)), "steps_f64": res[0][1],
-                           "steps_f16n": res[2][1], "seconds_f64": res[0][2], "seconds_f16n": res[2][2]}}
+                           "criterion": "FP64 |dNu| <= 1e-6 Nu / 4000 steps; FP16N time to |dNu| <= 1e-4 Nu / "
+                                        "1000 steps, Nu = mean over the 20,000 steps after FP64's step count",
+                           "nu_f64": [float(x) for x in nu64], "nu_f16n": [float(x) for x in nu16],
+                           "max_rel_nu_error": float(np.nanmax(err)), "steps_f64": steps64,
+                           "steps_f16n": steps16, "seconds_f64": sec64, "seconds_f16n": sec16}}
 
 
 def warm_start_form(clb, torch, ncase=4):
@@ -502,7 +533,8 @@ def run_ours(args):
         bpn = FORMS[args.precision][1]
         gb = bpn * cells / per_launch / 1e9
         roof = {"bound": "hbm", "achieved": gb, "peak": hbm_peak, "unit": "GB/s", "frac": gb / hbm_peak,
-                "traffic": None, "kernel": f"k_step<{args.precision}>", "bytes_per_ccu": bpn,
+                "traffic": FORMS_DRAM_PER_NODE[args.precision] * cells,
+                "kernel": f"k_step2<{args.precision}>", "bytes_per_ccu": bpn,
                 "peak_source": f"{src} hbm_gbs"}
     elif FP64_FLOP_PER_CCU:
         ach = FP64_FLOP_PER_CCU * cells / per_launch / 1e12
