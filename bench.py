@@ -125,6 +125,23 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(seconds: float, dist=None, device: str = "cuda") -> float:
+    """The largest of the ranks' times, on every rank (the job ends with its
+    slowest replica); `seconds` itself without a process group."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(cells: int, steps: int, world: int, seconds: float) -> float:
+    """Node updates of all replicas (each advances `cells` nodes `steps`
+    times) per second of the slowest one, in millions."""
+    return cells * steps * world / seconds / 1e6
+
+
 def _porosity():
     from paper_2110_05943_gb300.inputs import porosity_field
     return porosity_field(NX, NY, seed=PHI_SEED, ell=PHI_ELL)
@@ -482,12 +499,9 @@ def run_ours(args):
     t = t_start.elapsed_time(t_end) / 1e3
     nu = sim.nusselt(clb.W)
     sim.close()
-    if dist is not None:
-        tt = torch.tensor([t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(t, dist)
     cells = NX * NY
-    value = cells * args.steps * ws / t / 1e6
+    value = whole_job_mlups(cells, args.steps, ws, t)
     per_launch = t / args.steps
 
     # end to end through the C ABI with pinned host buffers
@@ -513,11 +527,8 @@ def run_ours(args):
         L.clb_destroy(h)
         te = time.perf_counter() - t0
         barrier()
-        if dist is not None:
-            tt = torch.tensor([te], device="cuda", dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            te = float(tt.item())
-        e2e = {"value": cells * args.steps * ws / te / 1e6, "unit": UNIT,
+        te = max_over_ranks(te, dist)
+        e2e = {"value": whole_job_mlups(cells, args.steps, ws, te), "unit": UNIT,
                "h2d_bytes_per_step": phi.nbytes / args.steps,
                "d2h_bytes_per_step": (4 * cells * 8 + 8) / args.steps,
                "includes": "clb_init (allocation + porosity upload) + steps + clb_macros + clb_nusselt"}
