@@ -334,24 +334,33 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __nv_bfloat16* __r
     }
     const uint32_t idesc = tc_idesc(ntp);
     const int nchunks = (K + TC_K - 1) / TC_K;
+    // A row tid of chunk c: TC_KV 16-byte K vectors, loaded one chunk ahead
+    // into registers so their latency overlaps the barrier, the MMAs and the
+    // next wait
+    uint4 va[TC_KV];
+    auto load_a = [&](int c) {
+#pragma unroll
+        for (int kv = 0; kv < TC_KV; ++kv) {
+            const int k = c * TC_K + 8 * kv;
+            va[kv] = make_uint4(0u, 0u, 0u, 0u);
+            if (k < K) {
+                const int tap = k / C, ch = k - tap * C;
+                const int yy = ry + sg * tap_dy(tap, s.taps), xx = rx + sg * tap_dx(tap, s.taps);
+                if (yy >= 0 && yy < s.h && xx >= 0 && xx < s.w)
+                    va[kv] = __ldg(reinterpret_cast<const uint4*>(A + ((rb + yy) * s.w + xx) * C + ch));
+            }
+        }
+    };
+    load_a(0);
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
         const int bi = c & 1;
         if (c >= 2 && ok) ok = mbar_wait(smem_u32(&mbar[bi]), ((c - 2) >> 1) & 1);
         const int k0 = c * TC_K;
-        // A: row tid, eight 16-byte K vectors
 #pragma unroll
-        for (int kv = 0; kv < TC_KV; ++kv) {
-            const int k = k0 + 8 * kv;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (k < K) {
-                const int tap = k / C, ch = k - tap * C;
-                const int yy = ry + sg * tap_dy(tap, s.taps), xx = rx + sg * tap_dx(tap, s.taps);
-                if (yy >= 0 && yy < s.h && xx >= 0 && xx < s.w)
-                    v = __ldg(reinterpret_cast<const uint4*>(A + ((rb + yy) * s.w + xx) * C + ch));
-            }
-            *reinterpret_cast<uint4*>(a_base + bi * TC_A_BYTES + (tid >> 3) * TC_ROWS8 + kv * 128 + (tid & 7) * 16) = v;
-        }
+        for (int kv = 0; kv < TC_KV; ++kv)
+            *reinterpret_cast<uint4*>(a_base + bi * TC_A_BYTES + (tid >> 3) * TC_ROWS8 + kv * 128 + (tid & 7) * 16) =
+                va[kv];
         // B: ntp rows, eight 16-byte K vectors each
         for (int e = tid; e < ntp * TC_KV; e += TC_THREADS) {
             const int r = e % ntp, kv = e / ntp, k = k0 + 8 * kv, gn = n0 + r;
@@ -366,6 +375,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __nv_bfloat16* __r
             }
             *reinterpret_cast<uint4*>(b_base + bi * b_bytes + (r >> 3) * TC_ROWS8 + kv * 128 + (r & 7) * 16) = v;
         }
+        if (c + 1 < nchunks) load_a(c + 1);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (tid == 0 && ok) {
@@ -485,10 +495,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __
     const uint32_t idesc = tc_idesc(ntp) | (1u << 15) | (1u << 16);     // A and B MN-major
     const int lbo_a = 128 * (TC_M / 8), lbo_b = 128 * (ntp / 8);
     const int nchunks = (ke - kb + TC_K - 1) / TC_K;
-    bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-        const int bi = c & 1;
-        if (c >= 2 && ok) ok = mbar_wait(smem_u32(&mbar[bi]), ((c - 2) >> 1) & 1);
+    // this thread's A vectors of chunk c (its pixel, its channel groups),
+    // loaded one chunk ahead into registers
+    constexpr int NA = TC_M / 8 / TC_PIX_STEP;
+    uint4 va[NA];
+    auto load_a = [&](int c) {
         const int p = kb + c * TC_K + kl;
         int pn = 0, py = -1000000, px = 0;
         if (p < ke) {
@@ -497,25 +508,51 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __
             py = rem / s.w;
             px = rem - py * s.w;
         }
-        unsigned char* const ab = a_base + bi * TC_A_BYTES + (kl >> 3) * lbo_a + (kl & 7) * 16;
 #pragma unroll
-        for (int j = 0; j < TC_M / 8 / TC_PIX_STEP; ++j) {
+        for (int j = 0; j < NA; ++j) {
             const int g = g0 + TC_PIX_STEP * j, m = m0 + 8 * g;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            va[j] = make_uint4(0u, 0u, 0u, 0u);
             if (m < M) {
                 const int tap = m / s.cin, ci = m - tap * s.cin;
                 const int yy = py + tap_dy(tap, s.taps), xx = px + tap_dx(tap, s.taps);
                 if (yy >= 0 && yy < s.h && xx >= 0 && xx < s.w)
-                    v = __ldg(reinterpret_cast<const uint4*>(X + ((pn * s.h + yy) * s.w + xx) * s.cin + ci));
+                    va[j] = __ldg(reinterpret_cast<const uint4*>(X + ((pn * s.h + yy) * s.w + xx) * s.cin + ci));
             }
-            *reinterpret_cast<uint4*>(ab + g * 128) = v;
         }
+    };
+    // and its B vectors (output gradient at its pixel, channel groups g0,
+    // g0 + TC_PIX_STEP, ... below ntp / 8), also one chunk ahead
+    constexpr int NB = 256 / 8 / TC_PIX_STEP;
+    uint4 vb[NB];
+    auto load_b = [&](int c) {
+        const int p = kb + c * TC_K + kl;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const int g = g0 + TC_PIX_STEP * j;
+            vb[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (p < ke && 8 * g < nt) vb[j] = __ldg(reinterpret_cast<const uint4*>(dY + p * s.cout + n0 + 8 * g));
+        }
+    };
+    if (nchunks > 0) {
+        load_a(0);
+        load_b(0);
+    }
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+        const int bi = c & 1;
+        if (c >= 2 && ok) ok = mbar_wait(smem_u32(&mbar[bi]), ((c - 2) >> 1) & 1);
+        unsigned char* const ab = a_base + bi * TC_A_BYTES + (kl >> 3) * lbo_a + (kl & 7) * 16;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) *reinterpret_cast<uint4*>(ab + (g0 + TC_PIX_STEP * j) * 128) = va[j];
         unsigned char* const bb = b_base + bi * b_bytes + (kl >> 3) * lbo_b + (kl & 7) * 16;
-        for (int g = g0; g < ntp / 8; g += TC_PIX_STEP) {
-            const int n = n0 + 8 * g;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (p < ke && 8 * g < nt) v = __ldg(reinterpret_cast<const uint4*>(dY + p * s.cout + n));
-            *reinterpret_cast<uint4*>(bb + g * 128) = v;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) {
+            const int g = g0 + TC_PIX_STEP * j;
+            if (g < ntp / 8) *reinterpret_cast<uint4*>(bb + g * 128) = vb[j];
+        }
+        if (c + 1 < nchunks) {
+            load_a(c + 1);
+            load_b(c + 1);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
