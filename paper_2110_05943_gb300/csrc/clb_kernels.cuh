@@ -454,6 +454,48 @@ CLB_HD void collide5(R (&g)[5], R n0, R T, R X, R Y, const PhysT<R>& P) {
     g[4] = R(0.5) * (n4 - n2);
 }
 
+// Rest-centred thermal representation (the FP16N form).  With q_i(u) =
+// g^eq_i(1, u) and the rest state g_rest = T0 q(0), a form that carries
+// g~ = g - g_rest and T~ = T - T0 never rounds an O(0.1..0.4) distribution
+// in FP32 (that rounding, state-correlated and integrated over long thermal
+// times, biased the steady temperature).  Exact identities used:
+//   g^eq_i(T, u) - T0 q_i(0) = T~ q_i(u) + T0 (q_i(u) - q_i(0))
+//     = T~ (sigma - 2 cT2) - T |u|^2                       (i = 0)
+//     = (T~ cT2 + T u_d (u_d +- 1)) / 2                     (i = 1..4, d = x, y)
+// and, the thermal collision being linear in (g, n0, T) at fixed u,
+//   collide(g~ + g_rest, n0~ + sigma T0, T~ + T0) - g_rest
+//     = collide(g~, n0~, T~) + T0 k(u),
+//   k_0 = -b |u|^2,  k_{1,3} = (b X^2 +- a X) / 2,  k_{2,4} = (b Y^2 +- a Y) / 2,
+// a = zeta_a, b = 1 - 2 (1 - zeta_a) with the shift and 1 without it.
+template <int I, typename R>
+CLB_HD R geqc_comp(R Tt, R X, R Y, R sigma, R cT2, R T0) {
+    const R T = Tt + T0;
+    if (I == 0) return fma(Tt, sigma - R(2) * cT2, -T * fma(X, X, Y * Y));
+    const R u = (I == 1 || I == 3) ? X : Y;
+    return R(0.5) * fma(Tt, cT2, T * (u * (u + R((I == 1 || I == 2) ? 1.0 : -1.0))));
+}
+
+template <typename R>
+CLB_HD void geq5c(R Tt, R X, R Y, R sigma, R cT2, R T0, R (&ge)[5]) {
+    ge[0] = geqc_comp<0>(Tt, X, Y, sigma, cT2, T0);
+    ge[1] = geqc_comp<1>(Tt, X, Y, sigma, cT2, T0);
+    ge[2] = geqc_comp<2>(Tt, X, Y, sigma, cT2, T0);
+    ge[3] = geqc_comp<3>(Tt, X, Y, sigma, cT2, T0);
+    ge[4] = geqc_comp<4>(Tt, X, Y, sigma, cT2, T0);
+}
+
+template <typename R, bool SHIFT>
+CLB_HD void collide5_centred(R (&g)[5], R n0t, R Tt, R X, R Y, R T0, const PhysT<R>& P) {
+    collide5<R, SHIFT>(g, n0t, Tt, X, Y, P);
+    const R a = R(1) - P.om_a, b = SHIFT ? fma(R(-2), P.om_a, R(1)) : R(1);
+    const R bX2 = b * X * X, bY2 = b * Y * Y, aX = a * X, aY = a * Y, hT0 = R(0.5) * T0;
+    g[0] = fma(-T0, bX2 + bY2, g[0]);
+    g[1] = fma(hT0, bX2 + aX, g[1]);
+    g[3] = fma(hT0, bX2 - aX, g[3]);
+    g[2] = fma(hT0, bY2 + aY, g[2]);
+    g[4] = fma(hT0, bY2 - aY, g[4]);
+}
+
 // Force of Eq. 4 at a node whose velocity is imposed (wall nodes).
 template <typename R, bool FORCH>
 CLB_HD void force_at(R X, R Y, R T, R ayg, const CoefT<R>& c, const PhysT<R>& P, R& Fx, R& Fy) {
@@ -508,6 +550,7 @@ __device__ __forceinline__ constexpr bool column_dir(int i) { return i == 0 || i
 // writes a node's post-collision values (store) and gives the per-node
 // constants (coef).
 struct StoreF64 {
+    static constexpr bool kCentred = false;   // g and T carried as they are
     using R = double;
     using S = double;
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
@@ -556,6 +599,7 @@ __device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, const K
 }
 
 struct StoreH16 {
+    static constexpr bool kCentred = false;
     using R = float;
     using S = __half;
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
@@ -635,9 +679,9 @@ struct StoreH16 {
     }
 };
 
-// Baseline (rho, u, T, 1/phi) of the node whose record sits at plane offset o.
+// Baseline (rho, u, T - T0, 1/phi) of the node whose record sits at plane offset o.
 struct Base {
-    float rho, X, Y, T, ip;
+    float rho, X, Y, Tt, ip;
 };
 
 __device__ __forceinline__ Base load_base(const BufT<const __half>& B, const AuxT<float>& A,
@@ -649,7 +693,7 @@ __device__ __forceinline__ Base load_base(const BufT<const __half>& B, const Aux
     s.rho = 1.0f + a.x;
     s.X = a.y;
     s.Y = b.x;
-    s.T = K.T0 + b.y;
+    s.Tt = b.y;
     s.ip = __ldg(A.ip + o);
     return s;
 }
@@ -679,14 +723,6 @@ __device__ __forceinline__ R feq_comp(R rho, R X, R Y, R ip) {
     return R(0.25) * (fma(rho, fma(R(1.0 / 3.0), fma(R(sx), X, R(sy) * Y), R(1.0 / 9.0)), fma(A, t, Q)));
 }
 
-// One component of the thermal equilibrium (Eq. 34).
-template <int I, typename R>
-__device__ __forceinline__ R geq_comp(R T, R X, R Y, R sigma, R cT2) {
-    if (I == 0) return T * (sigma - fma(X, X, fma(Y, Y, R(2) * cT2)));
-    const R u = (I == 1 || I == 3) ? X : Y;
-    return T * fma(R(0.5) * u, u, fma(R((I == 1 || I == 2) ? 0.5 : -0.5), u, R(0.5) * cT2));
-}
-
 template <int I>
 __device__ __forceinline__ void pull_one(const BufT<const __half>& B, const AuxT<float>& A, const KParamsT<float>& K,
                                          const int (&o)[9], float (&f)[9], float (&g)[5], bool want_f, bool want_g) {
@@ -695,10 +731,11 @@ __device__ __forceinline__ void pull_one(const BufT<const __half>& B, const AuxT
     if (want_f) f[I] = fma(__half2float(__ldg(B.f + I * Q + o[I])), kDevInv, feq_comp<I>(s.rho, s.X, s.Y, s.ip));
     if (I < 5 && want_g)
         g[I < 5 ? I : 0] = fma(__half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o[I])), kDevInv,
-                               geq_comp<(I < 5 ? I : 0)>(s.T, s.X, s.Y, K.p.sigma, K.p.cT2));
+                               geqc_comp<(I < 5 ? I : 0)>(s.Tt, s.X, s.Y, K.p.sigma, K.p.cT2, K.T0));
 }
 
 struct StoreH16N {
+    static constexpr bool kCentred = true;    // g - g_rest(T0) and T - T0 (see geqc_comp)
     using R = float;
     using S = __half;
     static __device__ __forceinline__ void pull_all(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K,
@@ -736,21 +773,22 @@ struct StoreH16N {
                                                  uint32_t seq) {
         const int o = y * K.g.px + x, Q = (int)K.g.plane;
         const __half2 a = __floats2half2_rn(rho - 1.0f, X);
-        const __half2 b = __floats2half2_rn(Y, T - K.T0);
+        const __half2 b = __floats2half2_rn(Y, T);              // T: T - T0 in this form
         uint2 r;
         r.x = *reinterpret_cast<const unsigned int*>(&a);
         r.y = *reinterpret_cast<const unsigned int*>(&b);
         B.rec[o] = r;
         // same per-direction formulas, on the same rounded record, as pull_one
         const float2 fa = __half22float2(a), fb = __half22float2(b);
-        const float br = 1.0f + fa.x, bX = fa.y, bY = fb.x, bT = K.T0 + fb.y;
+        const float br = 1.0f + fa.x, bX = fa.y, bY = fb.x, bT = fb.y;
         const float fe[9] = {feq_comp<0>(br, bX, bY, ip), feq_comp<1>(br, bX, bY, ip), feq_comp<2>(br, bX, bY, ip),
                              feq_comp<3>(br, bX, bY, ip), feq_comp<4>(br, bX, bY, ip), feq_comp<5>(br, bX, bY, ip),
                              feq_comp<6>(br, bX, bY, ip), feq_comp<7>(br, bX, bY, ip), feq_comp<8>(br, bX, bY, ip)};
         const float s = K.p.sigma, c = K.p.cT2;
-        const float ge[5] = {geq_comp<0>(bT, bX, bY, s, c), geq_comp<1>(bT, bX, bY, s, c),
-                             geq_comp<2>(bT, bX, bY, s, c), geq_comp<3>(bT, bX, bY, s, c),
-                             geq_comp<4>(bT, bX, bY, s, c)};
+        const float t0 = K.T0;
+        const float ge[5] = {geqc_comp<0>(bT, bX, bY, s, c, t0), geqc_comp<1>(bT, bX, bY, s, c, t0),
+                             geqc_comp<2>(bT, bX, bY, s, c, t0), geqc_comp<3>(bT, bX, bY, s, c, t0),
+                             geqc_comp<4>(bT, bX, bY, s, c, t0)};
         const Dither d = dither_for((uint32_t)o, seq);
 #pragma unroll
         for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - fe[i]) * kDevScale, dbits(d, i));
@@ -793,9 +831,9 @@ struct StoreH16N {
         const f2 ipp = f2::make(ip.x, ip.y);
         f[I] = fma(f2::make(df.x, df.y), f2(kDevInv), feq_comp<I>(rho, X, Y, ipp));
         if (I < 5) {
-            const f2 T = f2(K.T0) + f2::make(b0.y, b1.y);
-            g[I < 5 ? I : 0] =
-                fma(f2::make(dg.x, dg.y), f2(kDevInv), geq_comp<(I < 5 ? I : 0)>(T, X, Y, f2(K.p.sigma), f2(K.p.cT2)));
+            const f2 Tt = f2::make(b0.y, b1.y);
+            g[I < 5 ? I : 0] = fma(f2::make(dg.x, dg.y), f2(kDevInv),
+                                   geqc_comp<(I < 5 ? I : 0)>(Tt, X, Y, f2(K.p.sigma), f2(K.p.cT2), f2(K.T0)));
         }
     }
     static __device__ __forceinline__ void pull2(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x0,
@@ -817,8 +855,9 @@ struct StoreH16N {
                                                   const f2 (&f)[9], const f2 (&g)[5], f2 rho, f2 X, f2 Y, f2 T, f2 ip,
                                                   uint32_t seq) {
         const int o = y * K.g.px + x0, Q = (int)K.g.plane;
-        const __half2 a0 = __floats2half2_rn(rho.lo() - 1.0f, X.lo()), b0 = __floats2half2_rn(Y.lo(), T.lo() - K.T0);
-        const __half2 a1 = __floats2half2_rn(rho.hi() - 1.0f, X.hi()), b1 = __floats2half2_rn(Y.hi(), T.hi() - K.T0);
+        // T: T - T0 in this form
+        const __half2 a0 = __floats2half2_rn(rho.lo() - 1.0f, X.lo()), b0 = __floats2half2_rn(Y.lo(), T.lo());
+        const __half2 a1 = __floats2half2_rn(rho.hi() - 1.0f, X.hi()), b1 = __floats2half2_rn(Y.hi(), T.hi());
         uint4 r;
         r.x = *reinterpret_cast<const unsigned int*>(&a0);
         r.y = *reinterpret_cast<const unsigned int*>(&b0);
@@ -828,13 +867,14 @@ struct StoreH16N {
         const float2 fa0 = __half22float2(a0), fb0 = __half22float2(b0);
         const float2 fa1 = __half22float2(a1), fb1 = __half22float2(b1);
         const f2 br = f2(1.0) + f2::make(fa0.x, fa1.x), bX = f2::make(fa0.y, fa1.y), bY = f2::make(fb0.x, fb1.x);
-        const f2 bT = f2(K.T0) + f2::make(fb0.y, fb1.y);
+        const f2 bT = f2::make(fb0.y, fb1.y), t0 = f2(K.T0);
         const f2 fe[9] = {feq_comp<0>(br, bX, bY, ip), feq_comp<1>(br, bX, bY, ip), feq_comp<2>(br, bX, bY, ip),
                           feq_comp<3>(br, bX, bY, ip), feq_comp<4>(br, bX, bY, ip), feq_comp<5>(br, bX, bY, ip),
                           feq_comp<6>(br, bX, bY, ip), feq_comp<7>(br, bX, bY, ip), feq_comp<8>(br, bX, bY, ip)};
         const f2 s = f2(K.p.sigma), c = f2(K.p.cT2);
-        const f2 ge[5] = {geq_comp<0>(bT, bX, bY, s, c), geq_comp<1>(bT, bX, bY, s, c), geq_comp<2>(bT, bX, bY, s, c),
-                          geq_comp<3>(bT, bX, bY, s, c), geq_comp<4>(bT, bX, bY, s, c)};
+        const f2 ge[5] = {geqc_comp<0>(bT, bX, bY, s, c, t0), geqc_comp<1>(bT, bX, bY, s, c, t0),
+                          geqc_comp<2>(bT, bX, bY, s, c, t0), geqc_comp<3>(bT, bX, bY, s, c, t0),
+                          geqc_comp<4>(bT, bX, bY, s, c, t0)};
         const Dither d0 = dither_for((uint32_t)o, seq), d1 = dither_for((uint32_t)o + 1U, seq);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
@@ -887,24 +927,30 @@ __device__ __forceinline__ void wall_state(const BufT<const typename P::S>& Bin,
                                            const KParamsT<typename P::R>& K, int x, int y, const WallInfo& w,
                                            const CoefT<typename P::R>& cb, typename P::R (&f)[9],
                                            typename P::R (&g)[5], typename P::R& rho, typename P::R& X,
-                                           typename P::R& Y, typename P::R& T, typename P::R& n0) {
+                                           typename P::R& Y, typename P::R& T, typename P::R& Tt,
+                                           typename P::R& n0) {
     using R = typename P::R;
+    // temperatures below are in the form's representation (T - T0 in the
+    // rest-centred form, T otherwise); T itself is returned for the force
     const int sx = x + w.dx, sy = y + w.dy;
     R fs[9], gs[5];
     P::pull(Bin, A, K, sx, sy, fs, gs);
     const Mom9T<R> ks = moments9(fs);
-    const R Ts = sum5(gs) * K.p.inv_sigma;
+    const R Tst = sum5(gs) * K.p.inv_sigma;
+    R Ts = Tst;
+    if constexpr (P::kCentred) Ts = R(K.T0) + Tst;
     const CoefT<R> cs = P::template coef<FORCH>(A, K, sx, sy);
     R Xs, Ys, Fxs, Fys;
     macro_velocity<R, FORCH>(ks.rho, ks.jx, ks.jy, Ts, A.ayg[sy], cs, K.p, Xs, Ys, Fxs, Fys);
-    R Tb;
+    R Tbt;
     if (w.st >= 0) {
-        Tb = K.b.Tw[w.st];
+        Tbt = K.b.Tw[w.st];
+        if constexpr (P::kCentred) Tbt = Tbt - R(K.T0);
     } else {
         R gss[5];
         P::pull5(Bin, A, K, x + 2 * w.dx, y + 2 * w.dy, gss);
-        const R Tss = sum5(gss) * K.p.inv_sigma;
-        Tb = (R(4) * Ts - Tss) * R(1.0 / 3.0);
+        const R Tsst = sum5(gss) * K.p.inv_sigma;
+        Tbt = (R(4) * Tst - Tsst) * R(1.0 / 3.0);
     }
     const R uw = K.b.uw[w.su], vw = K.b.vw[w.su];
     R fb[9], fe[9];
@@ -913,37 +959,49 @@ __device__ __forceinline__ void wall_state(const BufT<const typename P::S>& Bin,
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i] = fb[i] + (fs[i] - fe[i]);
     R gb[5], ge[5];
-    geq5(Tb, uw, vw, K.p.sigma, K.p.cT2, gb);
-    geq5(Ts, Xs, Ys, K.p.sigma, K.p.cT2, ge);
+    if constexpr (P::kCentred) {
+        geq5c(Tbt, uw, vw, K.p.sigma, K.p.cT2, R(K.T0), gb);
+        geq5c(Tst, Xs, Ys, K.p.sigma, K.p.cT2, R(K.T0), ge);
+    } else {
+        geq5(Tbt, uw, vw, K.p.sigma, K.p.cT2, gb);
+        geq5(Tst, Xs, Ys, K.p.sigma, K.p.cT2, ge);
+    }
 #pragma unroll
     for (int i = 0; i < 5; ++i) g[i] = gb[i] + (gs[i] - ge[i]);
     rho = ks.rho;
     X = uw;
     Y = vw;
-    T = Tb;
+    Tt = Tbt;
+    T = Tbt;
+    if constexpr (P::kCentred) T = R(K.T0) + Tbt;
     n0 = sum5(g);
 }
 
 // Macroscopic state of any node at the current time level (pre-collision
-// values in f, g; wall nodes rebuilt by non-equilibrium extrapolation).
+// values in f, g; wall nodes rebuilt by non-equilibrium extrapolation).  T
+// is the temperature, Tt and n0 = sigma Tt the form's representation of it
+// (equal to T and sum g unless the form is rest-centred).
 template <class P, bool FORCH>
 __device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin, const AuxT<typename P::R>& A,
                                            const KParamsT<typename P::R>& K, int x, int y,
                                            const CoefT<typename P::R>& c, typename P::R (&f)[9],
                                            typename P::R (&g)[5], Mom9T<typename P::R>& k, typename P::R& rho,
                                            typename P::R& X, typename P::R& Y, typename P::R& T,
-                                           typename P::R& Fx, typename P::R& Fy, typename P::R& n0) {
+                                           typename P::R& Tt, typename P::R& Fx, typename P::R& Fy,
+                                           typename P::R& n0) {
     using R = typename P::R;
     WallInfo w;
     if (!wall_info(K.g, K.b, x, y, w)) {
         P::pull(Bin, A, K, x, y, f, g);
         k = moments9(f);
         n0 = sum5(g);
-        T = n0 * K.p.inv_sigma;
+        Tt = n0 * K.p.inv_sigma;
+        T = Tt;
+        if constexpr (P::kCentred) T = R(K.T0) + Tt;
         rho = k.rho;
         macro_velocity<R, FORCH>(rho, k.jx, k.jy, T, A.ayg[y], c, K.p, X, Y, Fx, Fy);
     } else {
-        wall_state<P, FORCH>(Bin, A, K, x, y, w, c, f, g, rho, X, Y, T, n0);
+        wall_state<P, FORCH>(Bin, A, K, x, y, w, c, f, g, rho, X, Y, T, Tt, n0);
         k = moments9(f);
         force_at<R, FORCH>(X, Y, T, A.ayg[y], c, K.p, Fx, Fy);
     }
@@ -969,13 +1027,14 @@ __device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const B
     using R = typename P::R;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
     R f[9], g[5];
-    R rho, X, Y, T, Fx, Fy, n0;
+    R rho, X, Y, T, Tt, Fx, Fy, n0;
     Mom9T<R> k;
     const uint32_t seq = step_seq(in, out, x, y);
-    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Fx, Fy, n0);
+    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Tt, Fx, Fy, n0);
     collide9<R, SHIFT>(f, k, rho, X, Y, Fx, Fy, c.ip, K.p);
-    collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
-    P::store(out, K, x, y, f, g, rho, X, Y, T, c.ip, seq);
+    if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
+    else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
+    P::store(out, K, x, y, f, g, rho, X, Y, Tt, c.ip, seq);
 }
 
 template <class P, bool SHIFT, bool FORCH>
@@ -1007,12 +1066,15 @@ __device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const B
     P::pull2(as_const(in), A, K, x0, y, f, g);
     const Mom9T<f2> k = moments9(f);
     const f2 n0 = sum5(g);
-    const f2 T = n0 * P2.inv_sigma;
+    const f2 Tt = n0 * P2.inv_sigma;          // the form's representation of T
+    f2 T = Tt;
+    if constexpr (P::kCentred) T = f2(K.T0) + Tt;
     f2 X, Y, Fx, Fy;
     macro_velocity<f2, FORCH>(k.rho, k.jx, k.jy, T, f2(A.ayg[y]), c, P2, X, Y, Fx, Fy);
     collide9<f2, SHIFT>(f, k, k.rho, X, Y, Fx, Fy, c.ip, P2);
-    collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
-    P::store2(out, K, x0, y, f, g, k.rho, X, Y, T, c.ip, step_seq(in, out, x0, y));
+    if constexpr (P::kCentred) collide5_centred<f2, SHIFT>(g, n0, Tt, X, Y, f2(K.T0), P2);
+    else collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
+    P::store2(out, K, x0, y, f, g, k.rho, X, Y, Tt, c.ip, step_seq(in, out, x0, y));
 }
 
 template <class P, bool SHIFT, bool FORCH>
@@ -1082,9 +1144,9 @@ __global__ void k_macros(const BufT<typename P::S> in, const AuxT<typename P::R>
     if (x >= K.g.nx || y >= K.g.ny) return;
     const long long n = (long long)y * K.g.nx + x;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
-    R f[9], g[5], rho, X, Y, T, Fx, Fy, n0;
+    R f[9], g[5], rho, X, Y, T, Tt, Fx, Fy, n0;
     Mom9T<R> k;
-    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Fx, Fy, n0);
+    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Tt, Fx, Fy, n0);
     if (orho) orho[n] = (double)rho;
     if (oux) oux[n] = (double)X;
     if (ouy) ouy[n] = (double)Y;
@@ -1120,12 +1182,16 @@ __global__ void k_set_fields(const BufT<typename P::S> out, const AuxT<typename 
         f[i] = fe[i];
         if (i < 5) {
             R ge[5];
-            geq5(zT, zu, zv, K.p.sigma, K.p.cT2, ge);
+            if constexpr (P::kCentred)
+                geq5c((R)(T[z] - (double)K.T0), zu, zv, K.p.sigma, K.p.cT2, R(K.T0), ge);
+            else
+                geq5(zT, zu, zv, K.p.sigma, K.p.cT2, ge);
             g[i] = ge[i];
         }
     }
     const long long n = (long long)y * K.g.nx + x;
-    P::store(out, K, x, y, f, g, (R)rho[n], (R)ux[n], (R)uy[n], (R)T[n], P::template coef<false>(A, K, x, y).ip,
+    const R Tn = P::kCentred ? (R)(T[n] - (double)K.T0) : (R)T[n];   // the form's representation
+    P::store(out, K, x, y, f, g, (R)rho[n], (R)ux[n], (R)uy[n], Tn, P::template coef<false>(A, K, x, y).ip,
              out.seq ? *out.seq : 0U);
 }
 

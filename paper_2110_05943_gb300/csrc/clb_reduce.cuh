@@ -46,16 +46,18 @@ __device__ __forceinline__ double temperature_at(const BufT<const typename P::S>
     using R = typename P::R;
     WallInfo w;
     R v[5];
+    // a rest-centred form carries T - T0
+    const double toff = P::kCentred ? (double)K.T0 : 0.0;
     if (!wall_info(K.g, K.b, x, y, w)) {
         P::pull5(B, A, K, x, y, v);
-        return (double)(sum5(v) * K.p.inv_sigma);
+        return toff + (double)(sum5(v) * K.p.inv_sigma);
     }
     if (w.st >= 0) return (double)K.b.Tw[w.st];
     P::pull5(B, A, K, x + w.dx, y + w.dy, v);
     const R Ts = sum5(v) * K.p.inv_sigma;
     P::pull5(B, A, K, x + 2 * w.dx, y + 2 * w.dy, v);
     const R Tss = sum5(v) * K.p.inv_sigma;
-    return (double)((R(4) * Ts - Tss) * R(1.0 / 3.0));
+    return toff + (double)((R(4) * Ts - Tss) * R(1.0 / 3.0));
 }
 
 // Per-block partial sums of the trapezoid-weighted local Nusselt number
