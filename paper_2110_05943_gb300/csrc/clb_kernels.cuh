@@ -599,7 +599,9 @@ __device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, const K
 }
 
 struct StoreH16 {
-    static constexpr bool kCentred = false;
+    // g is carried rest-centred (g - g_rest(T0), T - T0): the stored
+    // deviations are exactly that, so no baseline is added or subtracted
+    static constexpr bool kCentred = true;
     using R = float;
     using S = __half;
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
@@ -616,7 +618,7 @@ struct StoreH16 {
         sources<int>(K.g, x, y, o);
         const int Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = fma(__half2float(__ldg(B.g + i * Q + o[i])), kDevInv, K.wg[i]);
+        for (int i = 0; i < 5; ++i) g[i] = __half2float(__ldg(B.g + i * Q + o[i])) * kDevInv;
     }
     static __device__ __forceinline__ void pull(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
                                                 int y, R (&f)[9], R (&g)[5]) {
@@ -630,7 +632,7 @@ struct StoreH16 {
 #pragma unroll
         for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - K.wf[i]) * kDevScale, dbits(d, i));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half((g[i] - K.wg[i]) * kDevScale, dbits(d, 9 + i));
+        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half(g[i] * kDevScale, dbits(d, 9 + i));
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
@@ -656,7 +658,7 @@ struct StoreH16 {
             float2 v;
             if (column_dir(i)) v = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.g + i * Q + o0[i])));
             else v = make_float2(__half2float(__ldg(B.g + i * Q + o0[i])), __half2float(__ldg(B.g + i * Q + o1[i])));
-            g[i] = fma(f2::make(v.x, v.y), f2(kDevInv), f2(K.wg[i]));
+            g[i] = f2::make(v.x, v.y) * f2(kDevInv);
         }
     }
     static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
@@ -672,7 +674,7 @@ struct StoreH16 {
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
-            const f2 d = (g[i] - f2(K.wg[i])) * f2(kDevScale);
+            const f2 d = g[i] * f2(kDevScale);
             *reinterpret_cast<__half2*>(B.g + i * Q + o) =
                 __halves2half2(sr_half(d.lo(), dbits(d0, 9 + i)), sr_half(d.hi(), dbits(d1, 9 + i)));
         }
