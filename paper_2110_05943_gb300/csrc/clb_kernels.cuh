@@ -133,7 +133,8 @@ __host__ __device__ inline BufT<const S> as_const(const BufT<S>& b) {
 // value to 1/128 of an FP16 unit in the last place (in FP16's normal range).
 // The bits come from the 32-bit integer mixer "lowbias32" (C. Wellons'
 // hash-prospector) keyed by the node's plane offset and the buffer's step
-// counter, so runs stay deterministic and bit-reproducible.
+// counter, stretched to three words by xorshift-multiply rounds, so runs
+// stay deterministic and bit-reproducible.
 CLB_HD uint32_t mix32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352dU;
@@ -150,8 +151,9 @@ struct Dither {
 CLB_HD Dither dither_for(uint32_t node, uint32_t seq) {
     Dither d;
     d.h[0] = mix32(node * 0x9E3779B1U ^ mix32(seq + 0x632BE5ABU));
-    d.h[1] = mix32(d.h[0] + 0x85EBCA77U);
-    d.h[2] = mix32(d.h[1] + 0xC2B2AE3DU);
+    // two more words by one xorshift-multiply round each (h[0] is already mixed)
+    d.h[1] = (d.h[0] ^ (d.h[0] >> 15)) * 0x85EBCA77U;
+    d.h[2] = (d.h[1] ^ (d.h[1] >> 13)) * 0xC2B2AE3DU;
     return d;
 }
 
@@ -159,6 +161,16 @@ CLB_HD uint32_t dbits(const Dither& d, int i) { return (d.h[i / 5] >> (6 * (i % 
 
 CLB_HD __half sr_half(float v, uint32_t r6) {
     return __float2half_rz(__uint_as_float(__float_as_uint(v) + ((r6 << 7) | 0x40U)));
+}
+
+// The same for a node pair in one packed conversion: lo -> .x, hi -> .y
+// (cvt.rz.f16x2.f32 puts its first source in the upper half).
+CLB_HD __half2 sr_half2(float lo, uint32_t rlo, float hi, uint32_t rhi) {
+    const float a = __uint_as_float(__float_as_uint(hi) + ((rhi << 7) | 0x40U));
+    const float b = __uint_as_float(__float_as_uint(lo) + ((rlo << 7) | 0x40U));
+    uint32_t r;
+    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
+    return *reinterpret_cast<const __half2*>(&r);
 }
 
 // Stored FP16 values are the deviations times 2^12 (exact): most
@@ -670,13 +682,13 @@ struct StoreH16 {
         for (int i = 0; i < 9; ++i) {
             const f2 d = (f[i] - f2(K.wf[i])) * f2(kDevScale);
             *reinterpret_cast<__half2*>(B.f + i * Q + o) =
-                __halves2half2(sr_half(d.lo(), dbits(d0, i)), sr_half(d.hi(), dbits(d1, i)));
+                sr_half2(d.lo(), dbits(d0, i), d.hi(), dbits(d1, i));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const f2 d = g[i] * f2(kDevScale);
             *reinterpret_cast<__half2*>(B.g + i * Q + o) =
-                __halves2half2(sr_half(d.lo(), dbits(d0, 9 + i)), sr_half(d.hi(), dbits(d1, 9 + i)));
+                sr_half2(d.lo(), dbits(d0, 9 + i), d.hi(), dbits(d1, 9 + i));
         }
     }
 };
@@ -882,13 +894,13 @@ struct StoreH16N {
         for (int i = 0; i < 9; ++i) {
             const f2 d = (f[i] - fe[i]) * f2(kDevScale);
             *reinterpret_cast<__half2*>(B.f + i * Q + o) =
-                __halves2half2(sr_half(d.lo(), dbits(d0, i)), sr_half(d.hi(), dbits(d1, i)));
+                sr_half2(d.lo(), dbits(d0, i), d.hi(), dbits(d1, i));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const f2 d = (g[i] - ge[i]) * f2(kDevScale);
             *reinterpret_cast<__half2*>(B.g + i * Q + o) =
-                __halves2half2(sr_half(d.lo(), dbits(d0, 9 + i)), sr_half(d.hi(), dbits(d1, 9 + i)));
+                sr_half2(d.lo(), dbits(d0, 9 + i), d.hi(), dbits(d1, 9 + i));
         }
     }
 };
