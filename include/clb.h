@@ -251,14 +251,18 @@ void clb_batch_destroy(clb_batch* b);
  * library's device memory, present on every GPU that loads the library
  * until the process exits, so walls longer than CLB_STATIC_MAX_WALL nodes
  * are rejected with CLB_ERR_ARG.  No cudaMalloc, cudaFree or allocating
- * library routine is called.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  All calls share the one array:
+ * library routine is called.  A call looks up the array's device address
+ * in the current context (cudaGetSymbolAddress, which allocates nothing)
+ * and caches it per device; a call whose stream is being captured uses
+ * that cache instead, so make one call on each device before any stream
+ * capture (a first call during capture fails with CLB_ERR_ARG).  All calls
+ * share the one array:
  * calls whose kernels can overlap on the GPU (different streams without
  * ordering between them) race and give wrong results.  Every slot a call
  * reads it has written itself, so nothing needs clearing between calls.
- * Errors: CLB_ERR_ARG (bad pointer, side or size), CLB_ERR_CUDA; message
- * in clb_last_error(NULL). */
+ * Errors: CLB_ERR_ARG (bad pointer, side or size), CLB_ERR_CUDA (also when
+ * a CUDA error from earlier work was already pending: it is reported and
+ * left in place); message in clb_last_error(NULL). */
 #define CLB_STATIC_MAX_PARTIALS 1024
 #define CLB_STATIC_MAX_WALL (CLB_STATIC_MAX_PARTIALS * 256)
 int clb_nusselt_field_static(const double* T, int32_t nx, int32_t ny, int32_t side, double L, double dT,

@@ -12,11 +12,12 @@
  * optimiser state are FP32.  Every call is asynchronous on `stream`
  * (cudaStream_t, NULL = legacy stream) and returns CLB_NOP_OK or an error;
  * shapes are checked on the host before any launch.  Products run on the
- * BF16 tensor cores with FP32 accumulation: the forward and input-gradient
- * convolutions on tcgen05 (accumulator in TMEM) whenever the gathered
+ * BF16 tensor cores with FP32 accumulation, on tcgen05 (accumulator in
+ * TMEM): the forward and input-gradient convolutions whenever the gathered
  * operand's channel count is a multiple of 8 and the operands are 16-byte
  * aligned (for the forward pass: when the transposed weights are given),
- * otherwise, and for the weight gradient, on mma.sync.
+ * the weight gradient whenever cin and cout are multiples of 8 and x, dy
+ * are 16-byte aligned; other shapes run on an mma.sync implicit GEMM.
  */
 #ifndef CLB_NOP_H
 #define CLB_NOP_H
@@ -93,6 +94,16 @@ int clb_nop_transpose(const void* w, void* wt, int32_t rows, int32_t cols, void*
  * time-out flag: CLB_NOP_ERR_TIMEOUT if a kernel gave up waiting for its
  * tensor-core operations (about 2 s) and skipped its output. */
 int clb_nop_check(void* stream);
+
+/* Failure-path self-test: one CTA takes TMEM, waits on an mbarrier that
+ * nothing arrives at for at most limit_cycles SM clock cycles (1 ..
+ * 4e9), then does what the tcgen05 kernels do when their tensor-core
+ * operations do not complete in time: sets the time-out flag, skips its
+ * output and frees the TMEM.  No tensor-core operation is issued and the
+ * context stays usable; a following clb_nop_check returns
+ * CLB_NOP_ERR_TIMEOUT (and clears the flag).  For tests of the failure
+ * detection. */
+int clb_nop_wait_selftest(int64_t limit_cycles, void* stream);
 
 /* Clear `bytes` bytes at ptr. */
 int clb_nop_zero(void* ptr, int64_t bytes, void* stream);

@@ -3,8 +3,13 @@
 //
 // The per-block partial sums live in a fixed array in this file's device
 // memory instead of a buffer obtained from cudaMalloc.  Host code cannot use
-// the array's name as a device address, so the address is looked up once per
-// device (cudaGetSymbolAddress, with that device current) and cached.
+// the array's name as a device address, so the address is looked up with
+// cudaGetSymbolAddress (which allocates nothing), with the device current.
+// A call made outside stream capture looks it up afresh -- after a
+// cudaDeviceReset or under another context of the same device the array
+// lives at a new address -- and caches it per device; a call made while its
+// stream is being captured uses that cache, because the lookup may have to
+// load the module, which capture does not allow.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -84,14 +89,22 @@ int fail(int code, const char* msg) {
     return code;
 }
 
-// Device address of s_partials on the current device, looked up on the
-// first call for that device.
-int scratch_address(double** out) {
+// Device address of s_partials in the current context: looked up afresh
+// unless the stream is being captured, then taken from the per-device cache.
+int scratch_address(cudaStream_t stream, double** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(CLB_ERR_CUDA, "clb_nusselt_field_static: cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices) return fail(CLB_ERR_ARG, "clb_nusselt_field_static: device index too large");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess)
+        return fail(CLB_ERR_CUDA, "clb_nusselt_field_static: cudaStreamIsCapturing failed");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
+    if (cap != cudaStreamCaptureStatusNone) {
+        if (!g_addr[dev])
+            return fail(CLB_ERR_ARG,
+                        "clb_nusselt_field_static: first call on this device made during stream capture; "
+                        "call it once before capturing");
+    } else {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, s_partials);
         if (e != cudaSuccess || !p) {
@@ -120,10 +133,19 @@ extern "C" int clb_nusselt_field_static(const double* T, int32_t nx, int32_t ny,
     const long long nb = (len + kThreads - 1) / kThreads;
     if (nb > CLB_STATIC_MAX_PARTIALS)
         return fail(CLB_ERR_ARG, "clb_nusselt_field_static: wall longer than CLB_STATIC_MAX_WALL nodes");
-    double* part = nullptr;
-    const int rc = scratch_address(&part);
-    if (rc != CLB_OK) return rc;
+    // an error left by earlier, unrelated work is reported as such and left
+    // in place for its owner (cudaGetLastError below would clear it)
+    const cudaError_t pending = cudaPeekAtLastError();
+    if (pending != cudaSuccess) {
+        char buf[256];
+        std::snprintf(buf, sizeof buf, "clb_nusselt_field_static: a CUDA error was pending before the call: %s",
+                      cudaGetErrorString(pending));
+        return fail(CLB_ERR_CUDA, buf);
+    }
     cudaStream_t s = (cudaStream_t)stream;
+    double* part = nullptr;
+    const int rc = scratch_address(s, &part);
+    if (rc != CLB_OK) return rc;
     const double scale = -L / dT / (double)(len - 1);
     k_nu_field_partial<<<(unsigned)nb, kThreads, 0, s>>>(T, nx, ny, side, scale, part);
     k_nu_field_sum<<<1, kThreads, 0, s>>>(part, (int)nb, nu);

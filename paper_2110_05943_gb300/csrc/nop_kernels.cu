@@ -246,8 +246,9 @@ __device__ __forceinline__ void mbar_init(uint32_t a) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
 }
 
-// Waits for completion `parity` of the mbarrier; false after the time limit.
-__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
+// Waits for completion `parity` of the mbarrier; false after `limit` SM
+// clock cycles.
+__device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity, long long limit = TC_TIMEOUT_CYCLES) {
     const long long t0 = clock64();
     while (true) {
         uint32_t done;
@@ -257,7 +258,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t a, uint32_t parity) {
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if (clock64() - t0 > TC_TIMEOUT_CYCLES) return false;
+        if (clock64() - t0 > limit) return false;
     }
 }
 
@@ -922,6 +923,47 @@ extern "C" int clb_nop_transpose(const void* w, void* wt, int32_t rows, int32_t 
     if (!w || !wt || rows < 1 || cols < 1) return CLB_NOP_ERR_ARG;
     k_transpose_bf16<<<nblk((long long)rows * cols), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)w,
                                                                                    (__nv_bfloat16*)wt, rows, cols);
+    return status();
+}
+
+namespace {
+// The tensor-core kernels' failure path on its own: one CTA allocates TMEM
+// and waits on an mbarrier that nothing arrives at, with a bound of `limit`
+// cycles; the wait expires, the threads agree on the outcome, thread 0 sets
+// the time-out flag and warp 0 frees the TMEM -- exactly what k_conv_tc and
+// k_wgrad_tc do when their MMAs do not complete in time.  No MMA is issued.
+__global__ void __launch_bounds__(TC_THREADS) k_wait_selftest(long long limit) {
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    constexpr uint32_t cols = 32;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    bool ok = mbar_wait(smem_u32(&mbar), 0u, limit);   // phase 0 never completes
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) atomicExch(&g_nop_timeout, 1u);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols) : "memory");
+}
+}  // namespace
+
+extern "C" int clb_nop_wait_selftest(int64_t limit_cycles, void* stream) {
+    if (limit_cycles < 1 || limit_cycles > TC_TIMEOUT_CYCLES) return CLB_NOP_ERR_ARG;
+    k_wait_selftest<<<1, TC_THREADS, 0, (cudaStream_t)stream>>>((long long)limit_cycles);
     return status();
 }
 

@@ -54,6 +54,7 @@ def _lib():
         L.clb_nop_zero.argtypes = [_VP, i64, _VP]
         L.clb_nop_transpose.argtypes = [_VP, _VP, i32, i32, _VP]
         L.clb_nop_check.argtypes = [_VP]
+        L.clb_nop_wait_selftest.argtypes = [i64, _VP]
         L.clb_nop_add_mask.argtypes = [_VP, _VP, _VP, _VP, i64, _VP]
         L._nop_ready = True
     return L

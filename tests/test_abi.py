@@ -97,3 +97,31 @@ def test_surrogate_entry_points_declared_and_reject_bad_shapes():
     assert lib.clb_nop_conv_fwd(fake, fake, None, None, fake, 0, 1, 1, 65536, 65536, 1, 1, 9, None) == -1
     assert lib.clb_nop_pool2(fake, fake, 1, 7, 8, 4, 0, None) == -1                            # odd height
     assert lib.clb_nop_adam(fake, fake, fake, fake, None, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == -1  # t = 0
+
+
+def test_non_finite_inputs_rejected_on_the_host():
+    """NaN or infinite porosity, parameters or row forces are argument
+    errors (CLB_ERR_ARG) found before any CUDA call, so they never reach a
+    kernel."""
+    import numpy as np
+    import pytest
+    from paper_2110_05943_gb300 import clb
+    bc = clb.clb_bc_cavity()
+    p = clb.clb_params_default(nx=16, ny=16)
+    for bad in (np.nan, np.inf, -np.inf, 0.0, -0.5):
+        phi = np.full(256, 0.5)
+        phi[37] = bad
+        with pytest.raises(clb.ClbError) as e:
+            clb.clb_init(p, phi, bc)
+        assert e.value.code == clb.CLB_ERR_ARG
+    for field in ("Ra", "Da", "Pr", "sigma", "dT", "s3", "varpi"):
+        q = clb.clb_params_default(nx=16, ny=16)
+        setattr(q, field, float("nan"))
+        with pytest.raises(clb.ClbError) as e:
+            clb.clb_init(q, np.full(256, 0.5), bc)
+        assert e.value.code == clb.CLB_ERR_ARG, field
+    ay = np.zeros(16)
+    ay[3] = np.nan
+    with pytest.raises(clb.ClbError) as e:
+        clb.clb_init(p, np.full(256, 0.5), bc, ay_row=ay)
+    assert e.value.code == clb.CLB_ERR_ARG

@@ -55,6 +55,7 @@ SHAPES = [  # n, h, w, cin, cout, taps: ragged against the 64 x 64 x 32 (mma.syn
     (1, 8, 8, 288, 96, 9),         # input gradient N = 288: two N tiles (256 + 32)
     (2, 10, 6, 24, 192, 9),
     (3, 16, 12, 48, 96, 9),
+    (16, 128, 128, 24, 24, 9),     # a production layer: the training batch at 128^2, 24 -> 24
 ]
 
 
@@ -266,3 +267,23 @@ def test_training_reduces_the_loss(lib):
     hist = surrogate.train(net, X, Y, epochs=40, batch=8, lr=2e-3)
     assert np.isfinite(hist[-1][0])
     assert hist[-1][0] < 0.25 * hist[0][0], (hist[0][0], hist[-1][0])
+
+
+def test_bounded_wait_expires_and_reports_timeout(lib):
+    """The tensor-core kernels' failure path, made to run: a CTA waits on an
+    mbarrier that nothing arrives at, with a bound of about 1 ms; the wait
+    expires, the CTA frees its TMEM and sets the flag, clb_nop_check reports
+    CLB_NOP_ERR_TIMEOUT once and clears it, and the context stays usable --
+    a convolution afterwards still matches the reference."""
+    assert lib.clb_nop_check(None) == 0
+    assert lib.clb_nop_wait_selftest(0, None) == -1                 # bound outside 1 .. 4e9
+    assert lib.clb_nop_wait_selftest(2_000_000, None) == 0
+    assert lib.clb_nop_check(None) == -3                            # CLB_NOP_ERR_TIMEOUT
+    assert lib.clb_nop_check(None) == 0                             # reported once, then cleared
+    n, h, w, cin, cout = 1, 16, 16, 24, 32
+    x, wm = _bf((n, h, w, cin), 41), _bf((9 * cin, cout), 42, 1 / 15)
+    xd, wd, wtd = x.cuda(), wm.cuda(), wm.t().contiguous().cuda()
+    y = torch.empty((n, h, w, cout), device="cuda")
+    assert lib.clb_nop_conv_fwd(_p(xd), _p(wd), _p(wtd), None, _p(y), 1, 0, n, h, w, cin, cout, 9, None) == 0
+    assert lib.clb_nop_check(None) == 0
+    _close(y.cpu(), _ref_conv(x, wm, 9, cin, cout), 1e-5)

@@ -43,6 +43,55 @@ def test_parity_cavity_64_uniform_10k_steps():
     assert abs(nu_g - nu_o) <= 1e-10 * abs(nu_o)
 
 
+def test_parity_seeded_porosity_cavity_10k_steps():
+    """The bar on seeded inputs: a 256 x 192 cavity whose porosity is the
+    workloads' seeded field 0.3 + 0.6 Phi(g) (Gaussian random field, here
+    with correlation length 16 cells), Ra 1e6, Da 1e-3, Pr 0.71, sigma 0.8,
+    Forchheimer term on; after 10,000 steps rho - 1, u_x, u_y and T match
+    the oracle within 1e-10, and so do the Nusselt numbers of all four
+    walls.  (Porosity varies node to node, so every phi factor of Eqs. 4, 5,
+    14, 19, 22-23 and A1 is exercised at a different value everywhere.)"""
+    import oracle
+    from paper_2110_05943_gb300.inputs import porosity_field
+    nx, ny = 256, 192
+    phi = porosity_field(nx, ny, seed=20211012, ell=16.0)
+    orc, sim = build(nx, ny, phi, Ra=1e6, Da=1e-3, Pr=0.71, sigma=0.8)
+    orc.step(10_000)
+    sim.step(10_000)
+    errs = _check(orc, sim)
+    print("seeded 256x192 cavity, 10,000 steps:", errs)
+    _, ux, _, T = orc.macros()
+    assert np.abs(ux).max() > 1e-3                     # a developed flow, not a field at rest
+    for side in range(4):
+        want = oracle.nusselt(T, side, orc.lat.L)
+        assert abs(sim.nusselt(side) - want) <= 1e-10 * max(1.0, abs(want)), side
+
+
+def test_divergent_run_reports_unstable():
+    """Failure detection: with the literal bulk rate s_b = s_v at the
+    4096^2 cavity's lattice parameters (s_v = 0.911 < 1.19, linearly
+    unstable) a 40^2 cavity blows up within a few hundred steps; the
+    host-side checks of clb_macros, clb_residual and clb_nusselt then return
+    CLB_ERR_UNSTABLE instead of non-finite numbers.  The handle stays
+    usable: a checkpoint taken before the blow-up restores finite fields."""
+    import oracle
+    from paper_2110_05943_gb300 import clb
+    sv = oracle.lattice_params(oracle.Problem(nx=40, ny=40, Ra=1e6, Da=1e-3, Pr=0.71, L=4095.0)).sv
+    p = clb.clb_params_default(nx=40, ny=40, Ra=1e6, Da=1e-3, Pr=0.71, L=4095.0, sb=sv)
+    sim = clb.Simulation.create(p, 0.6, clb.clb_bc_cavity(1.0, 0.0))
+    sim.step(50)
+    good = sim.get_state()
+    assert all(np.isfinite(a).all() for a in sim.macros())
+    sim.step(5000)
+    for call in (sim.macros, sim.residual, lambda: sim.nusselt(clb.W)):
+        with pytest.raises(clb.ClbError) as e:
+            call()
+        assert e.value.code == clb.CLB_ERR_UNSTABLE
+    sim.set_state(good)
+    assert all(np.isfinite(a).all() for a in sim.macros())
+    sim.close()
+
+
 def test_parity_random_porosity_ragged_grid():
     """Seeded Gaussian-random-field porosity, non-square grid with a ragged
     tile tail in x (300 = 2 x 128 + 44), Forchheimer on, sigma 0.8."""

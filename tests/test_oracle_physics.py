@@ -221,3 +221,82 @@ def test_cavity_nusselt_near_table1(orc):
     nu_e = orc.nusselt(T, orc.E, o.lat.L)
     assert abs(nu_w - 1.4873) < 0.03
     assert abs(nu_w - nu_e) < 0.02   # 0.014 on 32^2, 0.005 on 64^2 (T offset, O(Ma^2))
+
+
+# ------------------------------------------------------------ Nusselt number
+def _linear_in_normal(nx, ny, c, Lx):
+    """T(x, y) = 1 - x (1 + c y) / Lx: linear along x, so the one-sided
+    second-order difference at either W/E wall is exact, and the local
+    Nusselt number -L dT/dx = (1 + c y) L / Lx is linear along the wall, so
+    the trapezoid rule integrates it exactly."""
+    x = np.arange(nx, dtype=float)[None, :]
+    y = np.arange(ny, dtype=float)[:, None]
+    return 1.0 - x * (1.0 + c * y) / Lx
+
+
+@pytest.mark.parametrize("nx,ny,c", [(9, 7, 0.0), (9, 7, 0.125), (33, 5, -0.1)])
+def test_nusselt_of_fields_with_exact_derivative_and_integral(orc, nx, ny, c):
+    """Sec. 3.2's mean Nusselt number on fields where every discretisation
+    step is exact, so the closed form holds to rounding:
+    mean over the wall of (1 + c y) L / Lx = (1 + c (ny - 1) / 2) L / Lx.
+    A normalisation by n instead of n - 1 is off by 1/n (>= 3 %), a missing
+    end-point half weight by O(c), a first-order difference or a wrong sign
+    by O(1)."""
+    Lx, L = float(nx - 1), 10.0
+    T = _linear_in_normal(nx, ny, c, Lx)
+    want = (1.0 + c * (ny - 1) / 2.0) * L / Lx
+    for side, field in ((orc.W, T), (orc.E, T), (orc.S, T.T.copy()), (orc.N, T.T.copy())):
+        assert abs(orc.nusselt(field, side, L) - want) < 1e-13 * max(1.0, abs(want)), side
+    # dT scales the result inversely
+    assert abs(orc.nusselt(T, orc.W, L, dT=2.0) - want / 2.0) < 1e-13
+
+
+def test_nusselt_one_sided_difference_is_second_order_exact(orc):
+    """T = a + b x + q x^2 along the normal: the one-sided difference
+    (-3 T0 + 4 T1 - T2) / 2 equals the wall derivative b exactly; a
+    first-order difference would give b + q."""
+    nx, ny, a, b, q = 6, 5, 0.3, -0.07, 0.011
+    x = np.arange(nx, dtype=float)[None, :]
+    T = np.broadcast_to(a + b * x + q * x * x, (ny, nx)).copy()
+    assert abs(orc.nusselt(T, orc.W, 1.0) - (-b)) < 1e-15
+    # at the E wall (x = nx - 1) the derivative is b + 2 q (nx - 1)
+    assert abs(orc.nusselt(T, orc.E, 1.0) - (-(b + 2 * q * (nx - 1)))) < 1e-15
+
+
+@pytest.mark.parametrize("sigma,Pr", [(1.0, 1.0), (0.5, 0.71), (2.0, 3.0)])
+def test_pure_conduction_gives_nusselt_one(orc, sigma, Pr):
+    """Without buoyancy (g beta = 0: Ra = 0 with the viscosity fixed) the
+    fluid stays at rest and Eq. 3 reduces to steady conduction between the
+    isothermal walls: T is exactly linear, and the mean Nusselt number with
+    L = the wall distance is exactly 1 on both isothermal walls, whatever
+    sigma and the diffusivity.  The discrete steady state reproduces this to
+    rounding (a linear profile has a uniform non-equilibrium part, which the
+    extrapolation carries exactly; the adiabatic walls see no y gradient).
+    Checks the whole chain: D2Q5 collision, streaming, both wall rules and
+    the Nusselt post-processing, against a value fixed by the physics."""
+    nx, ny = 17, 8
+    p = orc.Problem(nx=nx, ny=ny, Ra=0.0, Da=1e-2, Pr=Pr, nu=0.1, sigma=sigma, L=nx - 1)
+    o = orc.Oracle(p, phi=0.6, nthreads=2)
+    o.step(int(60 * (nx - 1) ** 2 / o.lat.alpha_e / math.pi ** 2 * sigma) + 2000)
+    r, ux, uy, T = o.macros()
+    assert np.abs(ux).max() == 0.0 and np.abs(uy).max() == 0.0
+    x = np.arange(nx, dtype=float)[None, :]
+    assert np.abs(T - (1.0 - x / (nx - 1))).max() < 1e-12
+    assert abs(o.nusselt(orc.W) - 1.0) < 1e-11
+    assert abs(o.nusselt(orc.E) - 1.0) < 1e-11
+
+
+def test_pure_conduction_vertical_gives_nusselt_one(orc):
+    """The same with the isothermal walls at the bottom (T = 1) and top
+    (T = 0) and adiabatic side walls: the S/N branch of the Nusselt number
+    and the corner rule (an isothermal wall wins over an adiabatic one)."""
+    nx, ny = 6, 13
+    p = orc.Problem(nx=nx, ny=ny, Ra=0.0, Da=1e-2, Pr=1.0, nu=0.1, L=ny - 1,
+                    walls=orc.Walls(("wall",) * 4, (0.0,) * 4, (0.0,) * 4, (None, None, 1.0, 0.0)))
+    o = orc.Oracle(p, phi=0.8, nthreads=2)
+    o.step(8000)
+    _, ux, uy, T = o.macros()
+    y = np.arange(ny, dtype=float)[:, None]
+    assert np.abs(T - (1.0 - y / (ny - 1))).max() < 1e-12
+    assert abs(o.nusselt(orc.S) - 1.0) < 1e-11
+    assert abs(o.nusselt(orc.N) - 1.0) < 1e-11

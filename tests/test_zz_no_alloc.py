@@ -50,6 +50,32 @@ def test_static_nusselt_matches_clb_nusselt_on_consecutive_calls(torch):
     sim.close()
 
 
+def test_static_nusselt_on_a_caller_stream(torch):
+    """The stream argument is honoured: two calls in a row on a
+    non-default stream (ordered on it, so they share the scratch safely),
+    and only that stream is synchronised before the results are read."""
+    from paper_2110_05943_gb300 import clb
+    from paper_2110_05943_gb300.inputs import porosity_field
+    nx, ny = 130, 300                     # the W/E walls span two reduction blocks
+    phi = porosity_field(nx, ny, seed=5, ell=6.0)
+    _, sim = build(nx, ny, phi, Ra=1e5, Da=1e-2, Pr=0.71, with_oracle=False)
+    sim.step(300)
+    T = torch.empty((ny, nx), dtype=torch.float64, device="cuda")
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
+    clb.clb_macros_device(sim.handle, None, None, None, T.data_ptr())
+    torch.cuda.synchronize()              # T and out are ready before the other stream reads them
+    s = torch.cuda.Stream()
+    for k, side in enumerate((clb.W, clb.E)):
+        clb.clb_nusselt_field_static(T.data_ptr(), nx, ny, side, sim.lattice.L, 1.0, out.data_ptr() + 8 * k,
+                                     stream=s.cuda_stream)
+    s.synchronize()
+    got = out.cpu().numpy()
+    for k, side in enumerate((clb.W, clb.E)):
+        want = sim.nusselt(side)
+        assert abs(got[k] - want) <= TOL * max(1.0, abs(want)), (side, got[k], want)
+    sim.close()
+
+
 def test_static_nusselt_rejects_walls_beyond_its_scratch(torch):
     """A wall longer than CLB_STATIC_MAX_WALL nodes is refused on the host
     before any kernel is launched."""
