@@ -268,6 +268,15 @@ void clb_batch_destroy(clb_batch* b);
 int clb_nusselt_field_static(const double* T, int32_t nx, int32_t ny, int32_t side, double L, double dT,
                              double* nu, void* stream);
 
+/* Check of the FP64 step's own reciprocal and square root (hardware
+ * estimates refined by one third-order Newton-Raphson step) against CUDA's
+ * IEEE division and sqrt.  For each of the n device values x[i] > 0 it
+ * writes four device values out[4i .. 4i+3] = (step's 1/x, IEEE 1/x,
+ * step's sqrt(x), IEEE sqrt(x)); asynchronous on `stream`.  A diagnostic:
+ * the paper has no counterpart.  Errors: CLB_ERR_ARG, CLB_ERR_CUDA
+ * (message in clb_last_error(NULL)). */
+int clb_fp64_special_check(const double* x, int64_t n, double* out, void* stream);
+
 /* Last error message of h, or of the calling thread's last failed
  * clb_init when h is NULL. */
 const char* clb_last_error(const clb_handle* h);

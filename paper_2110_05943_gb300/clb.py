@@ -113,7 +113,8 @@ def load(build_if_needed: bool = True):
     for name in ("clb_batch_init", "clb_batch_step", "clb_batch_set_active", "clb_batch_tune", "clb_batch_nusselt",
                  "clb_batch_macros", "clb_batch_sync"):
         getattr(L, name).restype = ctypes.c_int
-    for name in ("clb_nusselt_field_static", "clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
+    L.clb_fp64_special_check.argtypes = [_VP, ctypes.c_int64, _VP, _VP]
+    for name in ("clb_fp64_special_check", "clb_nusselt_field_static", "clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
                  "clb_residual", "clb_lattice_params", "clb_get_state", "clb_set_state", "clb_sync"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -226,6 +227,11 @@ def clb_nusselt_field_static(T_ptr: int, nx: int, ny: int, side: int, L: float, 
     rc = load().clb_nusselt_field_static(T_ptr, int(nx), int(ny), int(side), float(L), float(dT), nu_ptr,
                                          _VP(stream) if stream else None)
     _check(rc, None)
+
+
+def clb_fp64_special_check(x_ptr: int, n: int, out_ptr: int, stream=None):
+    """Step's and IEEE reciprocal / square root of n device doubles (see clb.h)."""
+    _check(load().clb_fp64_special_check(x_ptr, int(n), out_ptr, _VP(stream) if stream else None), None)
 
 
 def clb_residual(h):

@@ -190,7 +190,7 @@ static int map_params(const clb_params* p, clb_lattice* lat, std::string& why) {
     return CLB_OK;
 }
 
-// Block shapes: 128 x 2 threads (FP64, one node each) and 16 x 8 threads
+// Block shapes: 64 x 2 threads (FP64, one node each) and 16 x 8 threads
 // (FP16, a node pair each: 32 x 8 nodes; taller blocks reuse the pulled rows
 // y - 1, y, y + 1 in L1, measured 3 % faster than 64 x 2 at 8192^2 F16N).  On
 // small grids the blocks shrink (to 64 threads at least) until there are two
@@ -211,7 +211,7 @@ static void shape_blocks(int units, int ny, int bx, int threads, dim3& block, di
 
 static void pick_launch(clb_handle* h) {
     const int nx = h->prm.nx, ny = h->prm.ny;
-    shape_blocks(nx, ny, 128, 256, h->block, h->grid);
+    shape_blocks(nx, ny, CLB_F64_BX, CLB_F64_THREADS, h->block, h->grid);
     shape_blocks((nx + 1) / 2, ny, 16, 128, h->block2, h->grid2);
 }
 
@@ -406,6 +406,12 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
         K.p.c6 = (1.0 - 0.5 * p->s3) / 3.0;
         K.p.ca = 1.0 - 0.5 * lat.sv;
         K.p.cb8 = 1.0 - 0.5 * p->s4;
+        K.p.sb3 = lat.sb / 3.0;
+        K.p.c62 = 2.0 * K.p.c6;
+        K.p.s49 = p->s4 / 9.0;
+        K.p.hza = 0.5 * lat.zeta_a;
+        K.p.hom = 0.5 * (1.0 - lat.zeta_a);
+        K.p.hcT2 = 0.5 * K.p.cT2;
         K.nuK = lat.nu / lat.K;
         K.l1c = p->forchheimer ? 0.875 / std::sqrt(150.0 * lat.K) : 0.0;
         K.T0 = p->T0;
@@ -465,16 +471,6 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
     CKI(cudaMalloc(&h->result, 8 * sizeof(double)));
     CKI(cudaMallocHost(&h->host_res, 8 * sizeof(double)));
 
-    // per-node constants (FP64 form) or FP32 porosity (FP16 form), staged
-    // through the scratch buffer
-    CKI(cudaMemcpyAsync(h->scratch, phi, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
-    if (half)
-        k_phi32<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, h->phi32, p->nx, p->ny, px,
-                                                                      h->prec == CLB_F16N);
-    else
-        k_coef<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, h->coef, n, lat.nu, lat.K,
-                                                                     p->forchheimer);
-    CKI(cudaGetLastError());
     // a_y per row with g beta T0 folded in: G_y = g beta T + (a_y - g beta T0)
     std::vector<double> ay(p->ny);
     for (int y = 0; y < p->ny; ++y) ay[y] = (ay_row ? ay_row[y] : p->ay) - lat.gbeta * p->T0;
@@ -483,6 +479,17 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
         CKI(cudaMemcpyAsync(h->ayg, ayf.data(), ayf.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
     else
         CKI(cudaMemcpyAsync(h->ayg, ay.data(), ay.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    // per-node constants (FP64 form) or FP32 porosity (FP16 form), staged
+    // through the scratch buffer
+    CKI(cudaMemcpyAsync(h->scratch, phi, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    if (half)
+        k_phi32<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, h->phi32, p->nx, p->ny, px,
+                                                                      h->prec == CLB_F16N);
+    else
+        k_coef<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->scratch, (const double*)h->ayg, h->coef,
+                                                                     p->nx, n, lat.nu, lat.K, p->ax, lat.gbeta,
+                                                                     p->forchheimer);
+    CKI(cudaGetLastError());
     CKI(cudaStreamSynchronize(h->stream));
 
     // start at rest: rho = 1, u = 0, T = T_init, filled on the device
@@ -713,6 +720,28 @@ extern "C" void clb_destroy(clb_handle* h) {
     cudaStreamSynchronize(h->stream);
     free_all(h);
     delete h;
+}
+
+// ------------------------------------------------------------------ checks
+namespace {
+__global__ void k_fp64_special_check(const double* __restrict__ x, long long n, double* __restrict__ out) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    out[4 * i + 0] = clb::recip(v);
+    out[4 * i + 1] = 1.0 / v;
+    out[4 * i + 2] = clb::sqroot(v);
+    out[4 * i + 3] = sqrt(v);
+}
+}  // namespace
+
+extern "C" int clb_fp64_special_check(const double* x, int64_t n, double* out, void* stream) {
+    if (!x || !out || n < 1) return fail(nullptr, CLB_ERR_ARG, "clb_fp64_special_check: bad arguments");
+    const long long nb = (n + 255) / 256;
+    if (nb > 0x7fffffffLL) return fail(nullptr, CLB_ERR_ARG, "clb_fp64_special_check: n too large");
+    k_fp64_special_check<<<(unsigned)nb, 256, 0, (cudaStream_t)stream>>>(x, n, out);
+    CK(nullptr, cudaGetLastError());
+    return CLB_OK;
 }
 
 // Message for clb_last_error(NULL) from entry points without a handle.

@@ -53,13 +53,20 @@ namespace clb {
 
 using ::fma;   // keep the float / double overloads visible next to fma(f2, f2, f2)
 
-// Per-node constants derived from the porosity (Eqs. 4, 5, 23).
+// Per-node constants derived from the porosity (Eqs. 4, 5, 23) and the
+// row's external force.  With them the half force of Eq. 4 is
+//   F / 2 = -(hdar + l1 |u|) u + (hgx, hgb T + hgy)
+// (G = (a_x, a_y + g beta (T - T0)), hgy carrying a_y - g beta T0).
 template <typename R>
-struct alignas(4 * sizeof(R)) CoefT {
+struct alignas(8 * sizeof(R)) CoefT {
     R ip;    // 1 / phi
-    R hphi;  // phi / 2
-    R dar;   // phi nu / K (Darcy coefficient of Eq. 4)
+    R l0;    // l0 = (1 + phi nu / (2 K)) / 2 (Eq. 23)
+    R l0sq;  // l0^2
     R aux;   // Forchheimer: l1 = phi F_phi / (2 sqrt K); else 1 / (2 l0)
+    R hdar;  // phi nu / (2 K): half the Darcy coefficient of Eq. 4
+    R hgx;   // phi a_x / 2
+    R hgb;   // phi g beta / 2
+    R hgy;   // phi (a_y - g beta T0) / 2 of the node's row
 };
 
 struct Geo {
@@ -81,6 +88,8 @@ struct PhysT {
     R sp, sm;                             // (s_b + s_v)/2, (s_b - s_v)/2: (k20, k02) block of Eq. 15
     R c6;                                 // (1 - s3/2) / 3  (Eq. 11 rows 6, 7 with Eq. 17)
     R ca, cb8;                            // unit-shift variant: 1 - s_v/2, 1 - s4/2
+    R sb3, c62, s49;                      // s_b / 3, 2 c6, s4 / 9
+    R hza, hom, hcT2;                     // zeta_a / 2, (1 - zeta_a) / 2, c_sT^2 / 2
 };
 
 template <typename R>
@@ -253,14 +262,39 @@ __device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) {
     return r;
 }
 
-// Reciprocal and square root: IEEE in FP64 (the parity path); in FP32 the
-// hardware approximations (relative error ~1e-7, far below the FP16 storage
-// resolution of the forms that compute in FP32).
-// FP64: IEEE division.  (A Newton-Raphson reciprocal seeded from the FP32
-// hardware reciprocal saves two DFMA per node but its FP64<->FP32
-// conversions cost more FP64-pipe time: measured 1.6 % slower.)
-CLB_HD double recip(double x) { return 1.0 / x; }
-CLB_HD double sqroot(double x) { return sqrt(x); }
+// Reciprocal and square root.
+// FP64: the hardware estimates rcp.approx.ftz.f64 / rsqrt.approx.ftz.f64
+// (relative error ~1e-6, measured) refined by one third-order Newton-Raphson
+// step (Newton's iteration with its second-order correction term, Householder
+// order 2):
+//   1/x       = r (1 + e + e^2),              e = 1 - x r,
+//   1/sqrt(s) = y (1 + e/2 + 3 e^2 / 8),      e = 1 - s y^2,   sqrt(s) = s / sqrt(s).
+// The error after the step is O(e^3) ~ 1e-18: the results are within 2 ulp
+// of the correctly rounded ones (checked on the GPU against CUDA's IEEE
+// division and sqrt).  They cost 3 and 6 FP64-pipe instructions against
+// ~6 and ~9.5 for the IEEE routines -- the FP64 step is bound by that pipe.
+// sqroot needs s > 0 (rsqrt(0) is infinite): callers add 1e-300, which
+// changes no square root of a representable velocity.
+// FP32: the hardware approximations (relative error ~1e-7, far below the
+// FP16 storage resolution of the forms that compute in FP32).
+CLB_HD double recip(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    const double e = fma(-x, r, 1.0);
+    return fma(r, fma(e, e, e), r);
+}
+CLB_HD double sqroot(double s) {
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(s));
+    const double e = fma(-s, y * y, 1.0);
+    const double sy = s * y;
+    return fma(sy * e, fma(0.375, e, 0.5), sy);
+}
+// Offset that keeps the argument of sqroot positive (FP64 only).
+template <typename R>
+CLB_HD R sqrt_guard() { return R(0); }
+template <>
+CLB_HD double sqrt_guard<double>() { return 1e-300; }
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ float sqroot(float x) {
     float r;
@@ -294,31 +328,30 @@ CLB_HD Mom9T<R> moments9(const R (&f)[9]) {
     return k;
 }
 
-// Macroscopic velocity by Eqs. 22-23 and force by Eq. 4 at a node with
-// density rho, momentum j = sum e f and temperature T.
+// Macroscopic velocity by Eqs. 22-23 and half the force of Eq. 4 at a node
+// with density rho, momentum j = sum e f and temperature T:
+//   v = j / rho + phi G / 2,  u = v / (l0 + sqrt(l0^2 + l1 |v|)),
+//   F / 2 = -(phi nu / (2 K) + l1 |u|) u + phi G / 2
+// (phi F_phi / sqrt(K) |u| u / 2 = l1 |u| u by the definition of l1).
 template <typename R, bool FORCH>
-CLB_HD void macro_velocity(R rho, R jx, R jy, R T, R ayg, const CoefT<R>& c, const PhysT<R>& P, R& X, R& Y, R& Fx,
-                           R& Fy) {
+CLB_HD void macro_velocity(R rho, R jx, R jy, R T, const CoefT<R>& c, R& X, R& Y, R& hFx, R& hFy) {
     const R irho = recip(rho);
-    const R Gy = fma(P.gbeta, T, ayg);           // a_y + g beta (T - T0), T0 folded into ayg
-    const R hGx = c.hphi * P.ax, hGy = c.hphi * Gy;
-    const R vx = fma(jx, irho, hGx), vy = fma(jy, irho, hGy);
-    R cF;
+    const R hGy = fma(c.hgb, T, c.hgy);
+    const R vx = fma(jx, irho, c.hgx), vy = fma(jy, irho, hGy);
+    R hcF;
     if (FORCH) {
-        const R l0 = fma(R(0.25), c.dar, R(0.5));
-        const R vm = sqroot(fma(vx, vx, vy * vy));
-        const R den = l0 + sqroot(fma(c.aux, vm, l0 * l0));
-        const R inv = recip(den);
+        const R vm = sqroot(fma(vx, vx, fma(vy, vy, sqrt_guard<R>())));
+        const R inv = recip(c.l0 + sqroot(fma(c.aux, vm, c.l0sq)));
         X = vx * inv;
         Y = vy * inv;
-        cF = fma(R(2) * c.aux, vm * inv, c.dar);   // phi nu/K + phi F_phi/sqrt(K) |u|
+        hcF = fma(c.aux, vm * inv, c.hdar);      // (phi nu/K + phi F_phi/sqrt(K) |u|) / 2
     } else {
         X = vx * c.aux;
         Y = vy * c.aux;
-        cF = c.dar;
+        hcF = c.hdar;
     }
-    Fx = fma(-cF, X, hGx + hGx);
-    Fy = fma(-cF, Y, hGy + hGy);
+    hFx = fma(-hcF, X, c.hgx);
+    hFy = fma(-hcF, Y, hGy);
 }
 
 // Porous flow equilibrium f^eq = M^-1 m^eq (Eq. 19).
@@ -356,17 +389,25 @@ CLB_HD void geq5(R T, R X, R Y, R sigma, R cT2, R (&ge)[5]) {
     ge[4] = R(0.5) * (n4 - n2);
 }
 
-// Flow collision (Eq. 11) in delta form; see the file comment.
+// Flow collision (Eq. 11) in delta form; see the file comment.  Result:
+// the raw-moment increments r = N^-1 Delta (Eq. A1; r_0 = 0), which
+// apply9 turns into f* = f + M^-1 r.  Inputs: the raw moments k of the
+// pre-collision f, rho, u = (X, Y), half the force hF = F / 2, 1/phi.
+template <typename R>
+struct Incr9T {
+    R r1, r2, r3, r4, r5, r6, r7, r8;
+};
+
 template <typename R, bool SHIFT>
-CLB_HD void collide9(R (&f)[9], const Mom9T<R>& k, R rho, R X, R Y, R Fx, R Fy, R ip, const PhysT<R>& P) {
-    const R rFx = rho * Fx, rFy = rho * Fy;
+CLB_HD Incr9T<R> collide9_incr(const Mom9T<R>& k, R rho, R X, R Y, R hFx, R hFy, R ip, const PhysT<R>& P) {
+    const R rhFx = rho * hFx, rhFy = rho * hFy;                  // S~1 / 2, S~2 / 2 (Eq. 17)
     const R px = fma(rho, X, -k.jx), py = fma(rho, Y, -k.jy);   // -(k~10), -(k~01)
     const R X2 = X * X, Y2 = Y * Y, XY = X * Y;
-    const R X2p = X + X, Y2p = Y + Y, XY4 = R(4) * XY;
-    const R r3 = rho * R(1.0 / 3.0), r9 = rho * R(1.0 / 9.0);
-    const R D1 = fma(R(0.5), rFx, px);
-    const R D2 = fma(R(0.5), rFy, py);
-    R r3v, r4v, r5v, r6v, r7v, r8v;
+    const R X2p = X + X, Y2p = Y + Y;
+    Incr9T<R> r;
+    r.r1 = px + rhFx;                                           // Delta_1 = -k~10 + S~1 / 2 (s_1 = 1)
+    r.r2 = py + rhFy;
+    const R D1 = r.r1, D2 = r.r2;
     if (SHIFT) {
         // central moments m~3..m~8 = rows 3..8 of N (Eq. 14) times m
         const R ipX = ip * X, ipY = ip * Y;
@@ -381,35 +422,40 @@ CLB_HD void collide9(R (&f)[9], const Mom9T<R>& k, R rho, R X, R Y, R Fx, R Fy, 
         const R c7 = fma(ipY, wp, fma(-X, k.k02, fma(-Y2p, k.k11, k.k12)));
         R A = Y2 * k.k20;
         A = fma(X2, k.k02, A);
-        A = fma(XY4, k.k11, A);
+        A = fma(R(4) * XY, k.k11, A);
         A = fma(-Y2p, k.k21, A);
         A = fma(-X2p, k.k12, A);
         A = fma(-(ip * XY), w + Xjy, A);
         const R c8 = fma(ip, A, k.k22);
-        // increments of Eq. 11 (Lambda of Eq. 15 with s_0 = s_1 = 1)
-        const R e3 = r3 - c3, e4 = r3 - c4;
-        const R D3 = fma(P.sp, e3, P.sm * e4);
-        const R D4 = fma(P.sp, e4, P.sm * e3);
+        // increments of Eq. 11 (Lambda of Eq. 15, s_0 = s_1 = 1); the
+        // (k20, k02) block relaxes towards rho / 3 each:
+        // D3 = s+ (rho/3 - c3) + s- (rho/3 - c4) = s_b rho / 3 - s+ c3 - s- c4
+        const R sbr = P.sb3 * rho;
+        const R D3 = fma(-P.sp, c3, fma(-P.sm, c4, sbr));
+        const R D4 = fma(-P.sp, c4, fma(-P.sm, c3, sbr));
         const R D5 = -P.sv * c5;
-        const R D6 = fma(-P.s3, c6, P.c6 * rFy);
-        const R D7 = fma(-P.s3, c7, P.c6 * rFx);
-        const R D8 = P.s4 * (r9 - c8);
+        const R D6 = fma(-P.s3, c6, P.c62 * rhFy);   // + (1 - s3/2) rho Fy / 3
+        const R D7 = fma(-P.s3, c7, P.c62 * rhFx);
+        const R D8 = fma(P.s49, rho, -P.s4 * c8);     // s4 (rho/9 - c8)
         // back to raw moments: N^-1 Delta (Eq. A1), Delta_0 = 0
         const R ipX2 = ipX + ipX, ipY2 = ipY + ipY;
-        r3v = fma(ipX2, D1, D3);
-        r4v = fma(ipY2, D2, D4);
-        r5v = fma(ipY, D1, fma(ipX, D2, D5));
-        r6v = fma(ipX, fma(Y2p, D1, X * D2), fma(Y, D3, fma(X2p, D5, D6)));
-        r7v = fma(ipY, fma(Y, D1, X2p * D2), fma(X, D4, fma(Y2p, D5, D7)));
+        const R XD2 = X * D2;
+        r.r3 = fma(ipX2, D1, D3);
+        r.r4 = fma(ipY2, D2, D4);
+        r.r5 = fma(ipY, D1, fma(ipX, D2, D5));
+        r.r6 = fma(ipX, fma(Y2p, D1, XD2), fma(Y, D3, fma(X2p, D5, D6)));
+        r.r7 = fma(ipY, fma(Y, D1, X2p * D2), fma(X, D4, fma(Y2p, D5, D7)));
         R B = Y2 * D3;
         B = fma(X2, D4, B);
-        B = fma(XY4, D5, B);
+        B = fma(R(4) * XY, D5, B);
         B = fma(Y2p, D6, B);
         B = fma(X2p, D7, B);
-        B = fma(R(2) * ip * XY, fma(Y, D1, X * D2), B);
-        r8v = fma(ip, B, D8);
+        B = fma(ipX2 * Y, fma(Y, D1, XD2), B);
+        r.r8 = fma(ip, B, D8);
     } else {
         // unit shift: relax raw moments towards Eq. 19's m^eq with Eq. 19's S
+        const R rFx = rhFx + rhFx, rFy = rhFy + rhFy;
+        const R r3 = rho * R(1.0 / 3.0), r9 = rho * R(1.0 / 9.0);
         const R ipr = ip * rho;
         const R meq3 = fma(ipr * X, X, r3), meq4 = fma(ipr * Y, Y, r3);
         const R meq5 = ipr * XY;
@@ -422,18 +468,23 @@ CLB_HD void collide9(R (&f)[9], const Mom9T<R>& k, R rho, R X, R Y, R Fx, R Fy, 
         const R S8 = R(2.0 / 3.0) * ip * fma(X, rFx, Y * rFy) + R(2) * ip * ip * XY * fma(Y, rFx, X * rFy);
         // (k20, k02) block: -Lambda_b (m - m^eq) + (I - Lambda_b / 2) S
         const R d3 = k.k20 - meq3, d4 = k.k02 - meq4;
-        r3v = -fma(P.sp, d3, P.sm * d4) + S3 - R(0.5) * fma(P.sp, S3, P.sm * S4);
-        r4v = -fma(P.sm, d3, P.sp * d4) + S4 - R(0.5) * fma(P.sm, S3, P.sp * S4);
-        r5v = fma(-P.sv, k.k11 - meq5, P.ca * S5);
-        r6v = fma(-P.s3, k.k21 - meq6, R(3) * P.c6 * S6);
-        r7v = fma(-P.s3, k.k12 - meq7, R(3) * P.c6 * S7);
-        r8v = fma(-P.s4, k.k22 - meq8, P.cb8 * S8);
+        r.r3 = -fma(P.sp, d3, P.sm * d4) + S3 - R(0.5) * fma(P.sp, S3, P.sm * S4);
+        r.r4 = -fma(P.sm, d3, P.sp * d4) + S4 - R(0.5) * fma(P.sm, S3, P.sp * S4);
+        r.r5 = fma(-P.sv, k.k11 - meq5, P.ca * S5);
+        r.r6 = fma(-P.s3, k.k21 - meq6, R(3) * P.c6 * S6);
+        r.r7 = fma(-P.s3, k.k12 - meq7, R(3) * P.c6 * S7);
+        r.r8 = fma(-P.s4, k.k22 - meq8, P.cb8 * S8);
     }
-    // f* = f + M^-1 r, r = (0, D1, D2, r3..r8)
-    const R pa = r3v - r8v, qa = D1 - r7v;
-    const R pb = r4v - r8v, qb = D2 - r6v;
-    const R u1 = r8v + r5v, u2 = r8v - r5v, v1 = r6v + r7v, v2 = r6v - r7v;
-    f[0] += (r8v - r3v) - r4v;
+    return r;
+}
+
+// f* = f + M^-1 r with r = (0, r1, ..., r8) (Eq. 13's M inverted).
+template <typename R>
+CLB_HD void apply9(R (&f)[9], const Incr9T<R>& r) {
+    const R pa = r.r3 - r.r8, qa = r.r1 - r.r7;
+    const R pb = r.r4 - r.r8, qb = r.r2 - r.r6;
+    const R u1 = r.r8 + r.r5, u2 = r.r8 - r.r5, v1 = r.r6 + r.r7, v2 = r.r6 - r.r7;
+    f[0] += (r.r8 - r.r3) - r.r4;
     f[1] = fma(R(0.5), pa + qa, f[1]);
     f[3] = fma(R(0.5), pa - qa, f[3]);
     f[2] = fma(R(0.5), pb + qb, f[2]);
@@ -444,26 +495,38 @@ CLB_HD void collide9(R (&f)[9], const Mom9T<R>& k, R rho, R X, R Y, R Fx, R Fy, 
     f[8] = fma(R(0.25), u2 - v2, f[8]);
 }
 
+template <typename R, bool SHIFT>
+CLB_HD void collide9(R (&f)[9], const Mom9T<R>& k, R rho, R X, R Y, R hFx, R hFy, R ip, const PhysT<R>& P) {
+    apply9(f, collide9_incr<R, SHIFT>(k, rho, X, Y, hFx, hFy, ip, P));
+}
+
 // Temperature collision (Eq. 28) with zeta_T = zeta_e = zeta_nu = 1:
 // g* = M_T^-1 N_T^-1 n~*, n~* = (sigma T, (1 - zeta_a) n~1, (1 - zeta_a) n~2,
 // c_sT^2 T, c_sT^2 T), where n~1 = n1 - u_x T (Eq. 31 with sigma T = n0).
-// Back-shifting (N_T^-1) gives n1* = u_x T + n~1*, n3* = u_x^2 T + 2 u_x n~1*
-// + c_sT^2 T.  The unit-shift variant relaxes the raw moments towards
-// Eq. 33 instead: n1* as above, n3* = (c_sT^2 + u_x^2) T.
+// Back-shifting (N_T^-1) gives n1* = u_x T + n~1* = zeta_a u_x T + (1 - zeta_a) n1
+// and n3* = u_x^2 T + 2 u_x n~1* + c_sT^2 T = (c_sT^2 - u_x^2) T + 2 u_x n1*.
+// The unit-shift variant relaxes the raw moments towards Eq. 33 instead:
+// n1* as above, n3* = (c_sT^2 + u_x^2) T.  M_T^-1 then gives
+// g0 = n0 - n3* - n4*, g1,3 = (n3* +- n1*) / 2, g2,4 = (n4* +- n2*) / 2;
+// the halves h = n* / 2 are formed directly.  Only n0, g1 - g3 and g2 - g4
+// of the pre-collision g are used.
 template <typename R, bool SHIFT>
 CLB_HD void collide5(R (&g)[5], R n0, R T, R X, R Y, const PhysT<R>& P) {
-    const R XT = X * T, YT = Y * T;
-    const R c1 = P.om_a * ((g[1] - g[3]) - XT);   // (1 - zeta_a) n~1
-    const R c2 = P.om_a * ((g[2] - g[4]) - YT);
-    const R n1 = XT + c1, n2 = YT + c2;
-    const R cT = P.cT2 * T;
-    const R n3 = SHIFT ? fma(X + X, c1, fma(X, XT, cT)) : fma(X, XT, cT);
-    const R n4 = SHIFT ? fma(Y + Y, c2, fma(Y, YT, cT)) : fma(Y, YT, cT);
-    g[0] = (n0 - n3) - n4;
-    g[1] = R(0.5) * (n1 + n3);
-    g[2] = R(0.5) * (n2 + n4);
-    g[3] = R(0.5) * (n3 - n1);
-    g[4] = R(0.5) * (n4 - n2);
+    const R h1 = fma(P.hom, g[1] - g[3], P.hza * (X * T));
+    const R h2 = fma(P.hom, g[2] - g[4], P.hza * (Y * T));
+    R h3, h4;
+    if (SHIFT) {
+        h3 = fma(X + X, h1, T * fma(R(-0.5) * X, X, P.hcT2));
+        h4 = fma(Y + Y, h2, T * fma(R(-0.5) * Y, Y, P.hcT2));
+    } else {
+        h3 = T * fma(R(0.5) * X, X, P.hcT2);
+        h4 = T * fma(R(0.5) * Y, Y, P.hcT2);
+    }
+    g[0] = fma(R(-2), h3 + h4, n0);
+    g[1] = h3 + h1;
+    g[3] = h3 - h1;
+    g[2] = h4 + h2;
+    g[4] = h4 - h2;
 }
 
 // Rest-centred thermal representation (the FP16N form).  With q_i(u) =
@@ -508,16 +571,14 @@ CLB_HD void collide5_centred(R (&g)[5], R n0t, R Tt, R X, R Y, R T0, const PhysT
     g[4] = fma(hT0, bY2 - aY, g[4]);
 }
 
-// Force of Eq. 4 at a node whose velocity is imposed (wall nodes).
+// Half the force of Eq. 4 at a node whose velocity is imposed (wall nodes).
 template <typename R, bool FORCH>
-CLB_HD void force_at(R X, R Y, R T, R ayg, const CoefT<R>& c, const PhysT<R>& P, R& Fx, R& Fy) {
-    const R Gy = fma(P.gbeta, T, ayg);
-    R cF = c.dar;
-    if (FORCH) cF = fma(R(2) * c.aux, sqroot(fma(X, X, Y * Y)), c.dar);
-    Fx = fma(-cF, X, R(2) * c.hphi * P.ax);
-    Fy = fma(-cF, Y, R(2) * c.hphi * Gy);
+CLB_HD void force_at(R X, R Y, R T, const CoefT<R>& c, R& hFx, R& hFy) {
+    R hcF = c.hdar;
+    if (FORCH) hcF = fma(c.aux, sqroot(fma(X, X, fma(Y, Y, sqrt_guard<R>()))), c.hdar);
+    hFx = fma(-hcF, X, c.hgx);
+    hFy = fma(-hcF, Y, fma(c.hgb, T, c.hgy));
 }
-
 
 template <typename R>
 __device__ __forceinline__ R sum5(const R (&v)[5]) {
@@ -528,9 +589,13 @@ __device__ __forceinline__ R sum5(const R (&v)[5]) {
 __device__ __forceinline__ CoefT<f2> pack_coef(const CoefT<float>& a, const CoefT<float>& b) {
     CoefT<f2> c;
     c.ip = f2::make(a.ip, b.ip);
-    c.hphi = f2::make(a.hphi, b.hphi);
-    c.dar = f2::make(a.dar, b.dar);
+    c.l0 = f2::make(a.l0, b.l0);
+    c.l0sq = f2::make(a.l0sq, b.l0sq);
     c.aux = f2::make(a.aux, b.aux);
+    c.hdar = f2::make(a.hdar, b.hdar);
+    c.hgx = f2::make(a.hgx, b.hgx);
+    c.hgb = f2::make(a.hgb, b.hgb);
+    c.hgy = f2::make(a.hgy, b.hgy);
     return c;
 }
 
@@ -550,6 +615,12 @@ __device__ __forceinline__ PhysT<f2> splat(const PhysT<float>& p) {
     q.c6 = f2(p.c6);
     q.ca = f2(p.ca);
     q.cb8 = f2(p.cb8);
+    q.sb3 = f2(p.sb3);
+    q.c62 = f2(p.c62);
+    q.s49 = f2(p.s49);
+    q.hza = f2(p.hza);
+    q.hom = f2(p.hom);
+    q.hcT2 = f2(p.hcT2);
     return q;
 }
 
@@ -563,6 +634,7 @@ __device__ __forceinline__ constexpr bool column_dir(int i) { return i == 0 || i
 // constants (coef).
 struct StoreF64 {
     static constexpr bool kCentred = false;   // g and T carried as they are
+    static constexpr bool kReload = true;     // interior f re-read before the update (see step_node)
     using R = double;
     using S = double;
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
@@ -584,6 +656,16 @@ struct StoreF64 {
         pull9(B, A, K, x, y, f);
         pull5(B, A, K, x, y, g);
     }
+    // The same nine values as pull9, loaded again (volatile: not merged
+    // with the first load, so f need not stay in registers in between).
+    static __device__ __forceinline__ void reload9(const BufT<const S>& B, const KParamsT<R>& K, int x, int y,
+                                                   R (&f)[9]) {
+        long long o[9];
+        sources<long long>(K.g, x, y, o);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(f[i]) : "l"(B.f + i * K.g.plane + o[i]));
+    }
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
                                                  const R (&f)[9], const R (&g)[5], R, R, R, R, R, uint32_t) {
         const long long o = (long long)y * K.g.px + x;
@@ -598,15 +680,21 @@ struct StoreF64 {
     }
 };
 
-// FP32 constants of a node from its porosity (Eqs. 4, 5, 23).
+// FP32 constants of a node from its porosity and its row's a_y - g beta T0
+// (Eqs. 4, 5, 23).
 template <bool FORCH>
-__device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, const KParamsT<float>& K) {
+__device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, float ayg, const KParamsT<float>& K) {
     CoefT<float> c;
+    const float hp = 0.5f * p;
     c.ip = ip;
-    c.hphi = 0.5f * p;
-    c.dar = p * K.nuK;
+    c.hdar = hp * K.nuK;
+    c.l0 = fmaf(0.5f, c.hdar, 0.5f);
+    c.l0sq = c.l0 * c.l0;
     // Ergun (Eq. 5): l1 = phi F_phi / (2 sqrt K) = 0.875 / sqrt(150 K phi)
-    c.aux = FORCH ? K.l1c * rsqrtf(p) : recip(1.0f + 0.5f * c.dar);
+    c.aux = FORCH ? K.l1c * rsqrtf(p) : recip(c.l0 + c.l0);
+    c.hgx = hp * K.p.ax;
+    c.hgb = hp * K.p.gbeta;
+    c.hgy = hp * ayg;
     return c;
 }
 
@@ -614,6 +702,7 @@ struct StoreH16 {
     // g is carried rest-centred (g - g_rest(T0), T - T0): the stored
     // deviations are exactly that, so no baseline is added or subtracted
     static constexpr bool kCentred = true;
+    static constexpr bool kReload = false;
     using R = float;
     using S = __half;
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
@@ -649,7 +738,7 @@ struct StoreH16 {
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
         const float p = __ldg(A.phi + y * K.g.nx + x);
-        return coef_from_phi<FORCH>(p, recip(p), K);
+        return coef_from_phi<FORCH>(p, recip(p), A.ayg[y], K);
     }
     // Two interior nodes (x0, x0 + 1), x0 even.
     static __device__ __forceinline__ void pull2(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x0,
@@ -750,6 +839,7 @@ __device__ __forceinline__ void pull_one(const BufT<const __half>& B, const AuxT
 
 struct StoreH16N {
     static constexpr bool kCentred = true;    // g - g_rest(T0) and T - T0 (see geqc_comp)
+    static constexpr bool kReload = false;
     using R = float;
     using S = __half;
     static __device__ __forceinline__ void pull_all(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K,
@@ -812,7 +902,7 @@ struct StoreH16N {
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
         const float ip = __ldg(A.ip + y * K.g.px + x);
-        return coef_from_phi<FORCH>(recip(ip), ip, K);
+        return coef_from_phi<FORCH>(recip(ip), ip, A.ayg[y], K);
     }
     // Two interior nodes (x0, x0 + 1), x0 even.
     template <int I>
@@ -954,8 +1044,8 @@ __device__ __forceinline__ void wall_state(const BufT<const typename P::S>& Bin,
     R Ts = Tst;
     if constexpr (P::kCentred) Ts = R(K.T0) + Tst;
     const CoefT<R> cs = P::template coef<FORCH>(A, K, sx, sy);
-    R Xs, Ys, Fxs, Fys;
-    macro_velocity<R, FORCH>(ks.rho, ks.jx, ks.jy, Ts, A.ayg[sy], cs, K.p, Xs, Ys, Fxs, Fys);
+    R Xs, Ys, hFxs, hFys;
+    macro_velocity<R, FORCH>(ks.rho, ks.jx, ks.jy, Ts, cs, Xs, Ys, hFxs, hFys);
     R Tbt;
     if (w.st >= 0) {
         Tbt = K.b.Tw[w.st];
@@ -1001,7 +1091,7 @@ __device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin,
                                            const CoefT<typename P::R>& c, typename P::R (&f)[9],
                                            typename P::R (&g)[5], Mom9T<typename P::R>& k, typename P::R& rho,
                                            typename P::R& X, typename P::R& Y, typename P::R& T,
-                                           typename P::R& Tt, typename P::R& Fx, typename P::R& Fy,
+                                           typename P::R& Tt, typename P::R& hFx, typename P::R& hFy,
                                            typename P::R& n0) {
     using R = typename P::R;
     WallInfo w;
@@ -1013,11 +1103,11 @@ __device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin,
         T = Tt;
         if constexpr (P::kCentred) T = R(K.T0) + Tt;
         rho = k.rho;
-        macro_velocity<R, FORCH>(rho, k.jx, k.jy, T, A.ayg[y], c, K.p, X, Y, Fx, Fy);
+        macro_velocity<R, FORCH>(rho, k.jx, k.jy, T, c, X, Y, hFx, hFy);
     } else {
         wall_state<P, FORCH>(Bin, A, K, x, y, w, c, f, g, rho, X, Y, T, Tt, n0);
         k = moments9(f);
-        force_at<R, FORCH>(X, Y, T, A.ayg[y], c, K.p, Fx, Fy);
+        force_at<R, FORCH>(X, Y, T, c, hFx, hFy);
     }
 }
 
@@ -1034,25 +1124,62 @@ __device__ __forceinline__ uint32_t step_seq(const BufT<S>& in, const BufT<S>& o
 }
 
 // One node's complete step: pull (or wall rebuild), macros, both collisions, store.
+// Interior nodes of a form with P::kReload drop f after taking its moments
+// and read it again from the input buffer (an L1/L2 hit) just before the
+// update f* = f + M^-1 r: nine loads instead of eighteen registers held
+// through the collision, which buys occupancy for the FP64-bound step.
 template <class P, bool SHIFT, bool FORCH>
 __device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
                                           const AuxT<typename P::R>& A, const KParamsT<typename P::R>& K, int x,
                                           int y) {
     using R = typename P::R;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
-    R f[9], g[5];
-    R rho, X, Y, T, Tt, Fx, Fy, n0;
-    Mom9T<R> k;
     const uint32_t seq = step_seq(in, out, x, y);
-    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Tt, Fx, Fy, n0);
-    collide9<R, SHIFT>(f, k, rho, X, Y, Fx, Fy, c.ip, K.p);
-    if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
-    else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
+    R f[9], g[5];
+    R rho, X, Y, T, Tt, hFx, hFy, n0;
+    WallInfo w;
+    if (!wall_info(K.g, K.b, x, y, w)) {
+        P::pull(as_const(in), A, K, x, y, f, g);
+        const Mom9T<R> k = moments9(f);
+        n0 = sum5(g);
+        Tt = n0 * K.p.inv_sigma;
+        T = Tt;
+        if constexpr (P::kCentred) T = R(K.T0) + Tt;
+        rho = k.rho;
+        macro_velocity<R, FORCH>(rho, k.jx, k.jy, T, c, X, Y, hFx, hFy);
+        const Incr9T<R> r = collide9_incr<R, SHIFT>(k, rho, X, Y, hFx, hFy, c.ip, K.p);
+        if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
+        else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
+        if constexpr (P::kReload) P::reload9(as_const(in), K, x, y, f);
+        apply9(f, r);
+    } else {
+        wall_state<P, FORCH>(as_const(in), A, K, x, y, w, c, f, g, rho, X, Y, T, Tt, n0);
+        const Mom9T<R> k = moments9(f);
+        force_at<R, FORCH>(X, Y, T, c, hFx, hFy);
+        collide9<R, SHIFT>(f, k, rho, X, Y, hFx, hFy, c.ip, K.p);
+        if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
+        else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
+    }
     P::store(out, K, x, y, f, g, rho, X, Y, Tt, c.ip, seq);
 }
 
+// FP64 step launch shape: threads per block (x extent CLB_F64_BX) and the
+// resident blocks per SM the register allocation is capped for.  Measured
+// at 4096^2 (GB300): 128 threads, 5 blocks (<= 96 registers, 20 warps/SM)
+// 2.98 GLUPS; 256 x 2 blocks 2.97; 6 or 7 blocks of 128 spill and run at
+// 2.88 / 2.96.
+#ifndef CLB_F64_THREADS
+#define CLB_F64_THREADS 128
+#endif
+#ifndef CLB_F64_MINB
+#define CLB_F64_MINB 5
+#endif
+#ifndef CLB_F64_BX
+#define CLB_F64_BX 64
+#endif
+
 template <class P, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(256) k_step(const BufT<typename P::S> in, const BufT<typename P::S> out,
+__global__ void __launch_bounds__(CLB_F64_THREADS, CLB_F64_MINB) k_step(const BufT<typename P::S> in, const BufT<typename P::S> out,
                                               const AuxT<typename P::R> A, const KParamsT<typename P::R> K) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1083,9 +1210,9 @@ __device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const B
     const f2 Tt = n0 * P2.inv_sigma;          // the form's representation of T
     f2 T = Tt;
     if constexpr (P::kCentred) T = f2(K.T0) + Tt;
-    f2 X, Y, Fx, Fy;
-    macro_velocity<f2, FORCH>(k.rho, k.jx, k.jy, T, f2(A.ayg[y]), c, P2, X, Y, Fx, Fy);
-    collide9<f2, SHIFT>(f, k, k.rho, X, Y, Fx, Fy, c.ip, P2);
+    f2 X, Y, hFx, hFy;
+    macro_velocity<f2, FORCH>(k.rho, k.jx, k.jy, T, c, X, Y, hFx, hFy);
+    collide9<f2, SHIFT>(f, k, k.rho, X, Y, hFx, hFy, c.ip, P2);
     if constexpr (P::kCentred) collide5_centred<f2, SHIFT>(g, n0, Tt, X, Y, f2(K.T0), P2);
     else collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
     P::store2(out, K, x0, y, f, g, k.rho, X, Y, Tt, c.ip, step_seq(in, out, x0, y));
@@ -1158,9 +1285,9 @@ __global__ void k_macros(const BufT<typename P::S> in, const AuxT<typename P::R>
     if (x >= K.g.nx || y >= K.g.ny) return;
     const long long n = (long long)y * K.g.nx + x;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
-    R f[9], g[5], rho, X, Y, T, Tt, Fx, Fy, n0;
+    R f[9], g[5], rho, X, Y, T, Tt, hFx, hFy, n0;
     Mom9T<R> k;
-    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Tt, Fx, Fy, n0);
+    node_state<P, FORCH>(as_const(in), A, K, x, y, c, f, g, k, rho, X, Y, T, Tt, hFx, hFy, n0);
     if (orho) orho[n] = (double)rho;
     if (oux) oux[n] = (double)X;
     if (ouy) ouy[n] = (double)Y;
@@ -1219,22 +1346,27 @@ __global__ void k_fill4(double* __restrict__ d, long long n, double a, double b,
     d[3 * n + i] = e;
 }
 
-// Per-node FP64 constants from the porosity (Eqs. 4, 5, 23).
-__global__ void k_coef(const double* __restrict__ phi, CoefT<double>* __restrict__ coef, long long n, double nu,
-                       double K, int forch) {
+// Per-node FP64 constants from the porosity (Eqs. 4, 5, 23) and the row's
+// a_y - g beta T0 (ayg, one value per row).
+__global__ void k_coef(const double* __restrict__ phi, const double* __restrict__ ayg, CoefT<double>* __restrict__ coef,
+                       int nx, long long n, double nu, double K, double ax, double gbeta, int forch) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double p = phi[i];
+    const double p = phi[i], hp = 0.5 * p;
     CoefT<double> c;
     c.ip = 1.0 / p;
-    c.hphi = 0.5 * p;
-    c.dar = p * nu / K;
+    c.hdar = hp * nu / K;
+    c.l0 = 0.5 + 0.5 * c.hdar;                                   // Eq. 23
+    c.l0sq = c.l0 * c.l0;
     if (forch) {
         const double Fphi = 1.75 / sqrt(150.0 * p * p * p);      // Ergun, Eq. 5
         c.aux = 0.5 * p * Fphi / sqrt(K);                         // l1 of Eq. 23
     } else {
-        c.aux = 1.0 / (1.0 + 0.5 * c.dar);                        // 1 / (2 l0), Eq. 23
+        c.aux = 1.0 / (2.0 * c.l0);                               // 1 / (2 l0), Eq. 23
     }
+    c.hgx = hp * ax;
+    c.hgb = hp * gbeta;
+    c.hgy = hp * ayg[i / nx];
     coef[i] = c;
 }
 

