@@ -240,10 +240,14 @@ static void step_as(clb_handle* h, cudaStream_t s, const AuxT<typename P::R>& A,
     using S = typename P::S;
     const BufT<S> in = h->buf<S>(h->par), out = h->buf<S>(1 - h->par);
     const bool sh = h->prm.shift != 0, fo = h->prm.forchheimer != 0;
-    if (sh && fo) k_step<P, true, true><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
-    else if (sh) k_step<P, true, false><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
-    else if (fo) k_step<P, false, true><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
-    else k_step<P, false, false><<<h->grid, h->block, 0, s>>>(in, out, A, kp);
+    // interior tiles, then the wall nodes (see k_step)
+    const int tx = (int)h->grid.x, nt = (int)(h->grid.x * h->grid.y);
+    const int threads = (int)(h->block.x * h->block.y);
+    const unsigned nb = (unsigned)(nt + (wall_count(h->k64.g) + threads - 1) / threads);
+    if (sh && fo) k_step<P, true, true><<<nb, h->block, 0, s>>>(in, out, A, kp, tx, nt);
+    else if (sh) k_step<P, true, false><<<nb, h->block, 0, s>>>(in, out, A, kp, tx, nt);
+    else if (fo) k_step<P, false, true><<<nb, h->block, 0, s>>>(in, out, A, kp, tx, nt);
+    else k_step<P, false, false><<<nb, h->block, 0, s>>>(in, out, A, kp, tx, nt);
 }
 
 // FP16 forms: two nodes per thread (k_step2), grid over node pairs.

@@ -1129,38 +1129,77 @@ __device__ __forceinline__ uint32_t step_seq(const BufT<S>& in, const BufT<S>& o
 // update f* = f + M^-1 r: nine loads instead of eighteen registers held
 // through the collision, which buys occupancy for the FP64-bound step.
 template <class P, bool SHIFT, bool FORCH>
-__device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
+__device__ __forceinline__ void step_interior(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
+                                              const AuxT<typename P::R>& A, const KParamsT<typename P::R>& K,
+                                              int x, int y) {
+    using R = typename P::R;
+    const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
+    const uint32_t seq = step_seq(in, out, x, y);
+    R f[9], g[5];
+    P::pull(as_const(in), A, K, x, y, f, g);
+    const Mom9T<R> k = moments9(f);
+    const R n0 = sum5(g);
+    const R Tt = n0 * K.p.inv_sigma;
+    R T = Tt;
+    if constexpr (P::kCentred) T = R(K.T0) + Tt;
+    R X, Y, hFx, hFy;
+    macro_velocity<R, FORCH>(k.rho, k.jx, k.jy, T, c, X, Y, hFx, hFy);
+    const Incr9T<R> r = collide9_incr<R, SHIFT>(k, k.rho, X, Y, hFx, hFy, c.ip, K.p);
+    if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
+    else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
+    if constexpr (P::kReload) P::reload9(as_const(in), K, x, y, f);
+    apply9(f, r);
+    P::store(out, K, x, y, f, g, k.rho, X, Y, Tt, c.ip, seq);
+}
+
+template <class P, bool SHIFT, bool FORCH>
+__device__ __forceinline__ void step_wall(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
                                           const AuxT<typename P::R>& A, const KParamsT<typename P::R>& K, int x,
-                                          int y) {
+                                          int y, const WallInfo& w) {
     using R = typename P::R;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
     const uint32_t seq = step_seq(in, out, x, y);
     R f[9], g[5];
     R rho, X, Y, T, Tt, hFx, hFy, n0;
-    WallInfo w;
-    if (!wall_info(K.g, K.b, x, y, w)) {
-        P::pull(as_const(in), A, K, x, y, f, g);
-        const Mom9T<R> k = moments9(f);
-        n0 = sum5(g);
-        Tt = n0 * K.p.inv_sigma;
-        T = Tt;
-        if constexpr (P::kCentred) T = R(K.T0) + Tt;
-        rho = k.rho;
-        macro_velocity<R, FORCH>(rho, k.jx, k.jy, T, c, X, Y, hFx, hFy);
-        const Incr9T<R> r = collide9_incr<R, SHIFT>(k, rho, X, Y, hFx, hFy, c.ip, K.p);
-        if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
-        else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
-        if constexpr (P::kReload) P::reload9(as_const(in), K, x, y, f);
-        apply9(f, r);
-    } else {
-        wall_state<P, FORCH>(as_const(in), A, K, x, y, w, c, f, g, rho, X, Y, T, Tt, n0);
-        const Mom9T<R> k = moments9(f);
-        force_at<R, FORCH>(X, Y, T, c, hFx, hFy);
-        collide9<R, SHIFT>(f, k, rho, X, Y, hFx, hFy, c.ip, K.p);
-        if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
-        else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
-    }
+    wall_state<P, FORCH>(as_const(in), A, K, x, y, w, c, f, g, rho, X, Y, T, Tt, n0);
+    const Mom9T<R> k = moments9(f);
+    force_at<R, FORCH>(X, Y, T, c, hFx, hFy);
+    collide9<R, SHIFT>(f, k, rho, X, Y, hFx, hFy, c.ip, K.p);
+    if constexpr (P::kCentred) collide5_centred<R, SHIFT>(g, n0, Tt, X, Y, R(K.T0), K.p);
+    else collide5<R, SHIFT>(g, n0, T, X, Y, K.p);
     P::store(out, K, x, y, f, g, rho, X, Y, Tt, c.ip, seq);
+}
+
+template <class P, bool SHIFT, bool FORCH>
+__device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
+                                          const AuxT<typename P::R>& A, const KParamsT<typename P::R>& K, int x,
+                                          int y) {
+    WallInfo w;
+    if (!wall_info(K.g, K.b, x, y, w)) step_interior<P, SHIFT, FORCH>(in, out, A, K, x, y);
+    else step_wall<P, SHIFT, FORCH>(in, out, A, K, x, y, w);
+}
+
+// Number of wall nodes, and the i-th of them: the S and N rows first (if
+// walled), then the W and E columns without the corners already counted.
+__host__ __device__ inline long long wall_count(const Geo& G) {
+    long long n = 0;
+    if (G.wall_y) n += 2LL * G.nx;
+    if (G.wall_x) n += 2LL * (G.wall_y ? G.ny - 2 : G.ny);
+    return n;
+}
+
+__device__ __forceinline__ void wall_node(const Geo& G, int i, int& x, int& y) {
+    if (G.wall_y) {
+        if (i < G.nx) { x = i; y = 0; return; }
+        if (i < 2 * G.nx) { x = i - G.nx; y = G.ny - 1; return; }
+        i -= 2 * G.nx;
+        const int h = G.ny - 2;
+        x = i < h ? 0 : G.nx - 1;
+        y = 1 + (i < h ? i : i - h);
+        return;
+    }
+    x = i < G.ny ? 0 : G.nx - 1;
+    y = i < G.ny ? i : i - G.ny;
 }
 
 // FP64 step launch shape: threads per block (x extent CLB_F64_BX) and the
@@ -1178,13 +1217,31 @@ __device__ __forceinline__ void step_node(const BufT<typename P::S>& in, const B
 #define CLB_F64_BX 64
 #endif
 
+// One launch, two kinds of blocks, so that no warp mixes the interior and
+// the wall path: blocks [0, n_tiles) cover the grid in tiles_x x ... tiles
+// of blockDim nodes and skip wall nodes; the blocks after them take the
+// wall nodes, one per thread, in wall_node order.
 template <class P, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(CLB_F64_THREADS, CLB_F64_MINB) k_step(const BufT<typename P::S> in, const BufT<typename P::S> out,
-                                              const AuxT<typename P::R> A, const KParamsT<typename P::R> K) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= K.g.nx || y >= K.g.ny) return;
-    step_node<P, SHIFT, FORCH>(in, out, A, K, x, y);
+__global__ void __launch_bounds__(CLB_F64_THREADS, CLB_F64_MINB)
+    k_step(const BufT<typename P::S> in, const BufT<typename P::S> out, const AuxT<typename P::R> A,
+           const KParamsT<typename P::R> K, int tiles_x, int n_tiles) {
+    const int b = blockIdx.x;
+    if (b < n_tiles) {
+        const int x = (b % tiles_x) * blockDim.x + threadIdx.x;
+        const int y = (b / tiles_x) * blockDim.y + threadIdx.y;
+        if (x >= K.g.nx || y >= K.g.ny) return;
+        if ((K.g.wall_x && (x == 0 || x == K.g.nx - 1)) || (K.g.wall_y && (y == 0 || y == K.g.ny - 1))) return;
+        step_interior<P, SHIFT, FORCH>(in, out, A, K, x, y);
+    } else {
+        const long long i = (long long)(b - n_tiles) * (blockDim.x * blockDim.y) + threadIdx.y * blockDim.x +
+                            threadIdx.x;
+        if (i >= wall_count(K.g)) return;
+        int x, y;
+        wall_node(K.g, (int)i, x, y);
+        WallInfo w;
+        wall_info(K.g, K.b, x, y, w);
+        step_wall<P, SHIFT, FORCH>(in, out, A, K, x, y, w);
+    }
 }
 
 // FP16 forms, two nodes (x0, x0 + 1) per thread: interior pairs run the
