@@ -41,6 +41,7 @@ extern "C" {
 #define CLB_ERR_OOM (-3)      /* device or host allocation failed */
 #define CLB_ERR_UNSTABLE (-4) /* non-finite value found in the fields */
 #define CLB_ERR_STATE (-5)    /* checkpoint does not match this handle */
+#define CLB_ERR_TIMEOUT (-6)  /* a bounded wait on the GPU expired (persistent batch) */
 
 /* Sides, in this order everywhere: west (x = 0), east (x = nx-1),
  * south (y = 0), north (y = ny-1).  Gravity points along -y. */
@@ -214,12 +215,33 @@ void clb_destroy(clb_handle* h);
  * the single-case entry points.  The paper has no batched form; this is the
  * data-parallel way to run parameter studies such as its Table 1. */
 typedef struct clb_batch clb_batch;
+/* Launch modes of a batch (clb_batch_set_mode):
+ *   CLB_BATCH_GRAPH      : one launch per step, replayed from CUDA graphs
+ *                          of 32 steps (the default);
+ *   CLB_BATCH_PERSISTENT : one cooperative launch (all blocks resident)
+ *                          per 32 steps, itself captured in a CUDA graph,
+ *                          whose steps are separated by a grid barrier.  A
+ *                          barrier wait is bounded (about 2 s); if it
+ *                          expires the launch stops, and the next call that
+ *                          waits for the batch (clb_batch_sync,
+ *                          clb_batch_nusselt, clb_batch_macros,
+ *                          clb_batch_set_mode) returns CLB_ERR_TIMEOUT.
+ * Both modes give identical results. */
+enum { CLB_BATCH_GRAPH = 0, CLB_BATCH_PERSISTENT = 1 };
 int clb_batch_init(clb_batch** b, int32_t ncase, const clb_params* p, const double* const* phi, const clb_bc* bc,
                    void* stream);
 int clb_batch_step(clb_batch* b, int64_t n);
 int clb_batch_set_active(clb_batch* b, const int32_t* active);
 int clb_batch_tune(clb_batch* b, int32_t steps, int32_t* chosen);
 int clb_batch_set_tiling(clb_batch* b, int32_t choice);
+int clb_batch_set_mode(clb_batch* b, int32_t mode);
+/* Failure-path self-test of the persistent mode's grid barrier: runs one
+ * persistent step whose barrier waits for one block more than the launch
+ * has, bounded by limit_cycles SM clock cycles (1 .. 4e9).  The wait
+ * expires, every block returns, and the call reports CLB_ERR_TIMEOUT; the
+ * step wrote only the buffer not in use, so the batch's state and time are
+ * unchanged and the batch stays usable. */
+int clb_batch_barrier_selftest(clb_batch* b, int64_t limit_cycles);
 /* Mean Nusselt number of `side` for every case (host array of ncase values). */
 int clb_batch_nusselt(clb_batch* b, int32_t side, double* nu);
 /* Macroscopic fields of case c (host arrays of that case's ny*nx values). */

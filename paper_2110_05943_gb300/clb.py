@@ -22,6 +22,8 @@ CLB_ERR_CUDA = -2
 CLB_ERR_OOM = -3
 CLB_ERR_UNSTABLE = -4
 CLB_ERR_STATE = -5
+CLB_ERR_TIMEOUT = -6
+CLB_BATCH_GRAPH, CLB_BATCH_PERSISTENT = 0, 1
 W, E, S, N = 0, 1, 2, 3
 CLB_PERIODIC, CLB_WALL = 0, 1
 CLB_ADIABATIC, CLB_ISOTHERMAL = 0, 1
@@ -99,6 +101,8 @@ def load(build_if_needed: bool = True):
     L.clb_batch_set_active.argtypes = [_VP, ctypes.POINTER(ctypes.c_int32)]
     L.clb_batch_tune.argtypes = [_VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     L.clb_batch_set_tiling.argtypes = [_VP, ctypes.c_int32]
+    L.clb_batch_set_mode.argtypes = [_VP, ctypes.c_int32]
+    L.clb_batch_barrier_selftest.argtypes = [_VP, ctypes.c_int64]
     L.clb_batch_nusselt.argtypes = [_VP, ctypes.c_int32, _DP]
     L.clb_batch_macros.argtypes = [_VP, ctypes.c_int32, _DP, _DP, _DP, _DP]
     L.clb_batch_nodes.argtypes = [_VP]
@@ -111,7 +115,8 @@ def load(build_if_needed: bool = True):
     L.clb_batch_destroy.argtypes = [_VP]
     L.clb_batch_destroy.restype = None
     for name in ("clb_batch_init", "clb_batch_step", "clb_batch_set_active", "clb_batch_tune", "clb_batch_nusselt",
-                 "clb_batch_macros", "clb_batch_sync"):
+                 "clb_batch_macros", "clb_batch_sync", "clb_batch_set_tiling", "clb_batch_set_mode",
+                 "clb_batch_barrier_selftest"):
         getattr(L, name).restype = ctypes.c_int
     L.clb_fp64_special_check.argtypes = [_VP, ctypes.c_int64, _VP, _VP]
     for name in ("clb_fp64_special_check", "clb_nusselt_field_static", "clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
@@ -363,6 +368,15 @@ def clb_batch_set_tiling(b, choice: int):
     _bcheck(load().clb_batch_set_tiling(b, int(choice)), b)
 
 
+def clb_batch_set_mode(b, mode: int):
+    _bcheck(load().clb_batch_set_mode(b, int(mode)), b)
+
+
+def clb_batch_barrier_selftest(b, limit_cycles: int):
+    """Returns the library's status (CLB_ERR_TIMEOUT expected); see clb.h."""
+    return int(load().clb_batch_barrier_selftest(b, int(limit_cycles)))
+
+
 def clb_batch_tune(b, steps: int = 4) -> int:
     ch = ctypes.c_int32(-1)
     _bcheck(load().clb_batch_tune(b, int(steps), ctypes.byref(ch)), b)
@@ -419,6 +433,12 @@ class Batch:
 
     def set_tiling(self, choice: int):
         clb_batch_set_tiling(self.handle, choice)
+
+    def set_mode(self, mode: int):
+        clb_batch_set_mode(self.handle, mode)
+
+    def barrier_selftest(self, limit_cycles: int) -> int:
+        return clb_batch_barrier_selftest(self.handle, limit_cycles)
 
     def nusselt(self, side: int = W) -> np.ndarray:
         return clb_batch_nusselt(self.handle, len(self), side)

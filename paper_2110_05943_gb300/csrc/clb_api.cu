@@ -6,6 +6,7 @@
 // FP64 reductions for the Nusselt number and the steady-state residual.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdarg>
@@ -257,10 +258,15 @@ static void step2_as(clb_handle* h, cudaStream_t s) {
     const BufT<S> in = h->buf<S>(h->par), out = h->buf<S>(1 - h->par);
     const AuxT<float> A = h->aux32();
     const bool sh = h->prm.shift != 0, fo = h->prm.forchheimer != 0;
-    if (sh && fo) k_step2<P, true, true><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
-    else if (sh) k_step2<P, true, false><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
-    else if (fo) k_step2<P, false, true><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
-    else k_step2<P, false, false><<<h->grid2, h->block2, 0, s>>>(in, out, A, h->k32);
+    // pair tiles (interior pairs only), then the edge nodes (see k_step2)
+    const Geo& G = h->k32.g;
+    const int tx = (int)h->grid2.x, nt = (int)(h->grid2.x * h->grid2.y);
+    const int threads = (int)(h->block2.x * h->block2.y);
+    const unsigned nb = (unsigned)(nt + (edge_count(G) + threads - 1) / threads);
+    if (sh && fo) k_step2<P, true, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+    else if (sh) k_step2<P, true, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+    else if (fo) k_step2<P, false, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+    else k_step2<P, false, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
 }
 
 static void launch_step(clb_handle* h, cudaStream_t s) {
@@ -438,7 +444,10 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
         k.l1c = (float)K.l1c;
         k.T0 = (float)K.T0;
         const double w9[9] = {16.0 / 36, 4.0 / 36, 4.0 / 36, 4.0 / 36, 4.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-        for (int i = 0; i < 9; ++i) k.wf[i] = (float)w9[i];
+        for (int i = 0; i < 9; ++i) {
+            k.wf[i] = (float)w9[i];
+            k.wfs[i] = k.wf[i] * kDevScale;   // exact (power of two)
+        }
         k.wg[0] = (float)((p->sigma - p->varpi) * p->T0);
         for (int i = 1; i < 5; ++i) k.wg[i] = (float)(0.25 * p->varpi * p->T0);
     }

@@ -3,9 +3,14 @@
 //
 // Each case is an ordinary clb_handle (its own buffers, parameters and
 // reductions); the batch builds a device table of the cases and a tile list
-// over the active ones, and advances all of them with k_step_batch,
-// replayed from CUDA graphs of kGraphSteps steps.  Cases can be retired
-// (e.g. once steady) and the tile shape is chosen by a measured sweep.
+// over the active ones and advances all of them, in one of two modes:
+//   CLB_BATCH_GRAPH      : one k_step_batch launch per step, replayed from
+//                          CUDA graphs of kGraphSteps steps;
+//   CLB_BATCH_PERSISTENT : one cooperative k_step_batch_persist launch per
+//                          kGraphSteps steps (itself captured in a graph),
+//                          its steps separated by a bounded grid barrier.
+// Cases can be retired (e.g. once steady) and the tile shape is chosen by a
+// measured sweep.
 
 struct clb_batch {
     std::vector<clb_handle*> cases;
@@ -25,6 +30,10 @@ struct clb_batch {
     int per_cta = 8;                // tiles per CTA
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
+    int mode = CLB_BATCH_GRAPH;
+    GridBarrier* bar = nullptr;     // persistent mode: grid barrier state (device)
+    int pgrid = 0;                  // persistent mode: resident blocks of the launch
+    long long wait_limit = 4000000000LL;   // barrier wait bound, SM cycles (~2 s)
     std::string err;
 };
 
@@ -63,6 +72,7 @@ static void batch_drop_graphs(clb_batch* b) {
             b->graph[i] = nullptr;
         }
     b->graph_failed = false;
+    b->pgrid = 0;
 }
 
 static int nodes_per_thread(const clb_batch* b) { return b->prec == CLB_F64 ? 1 : 2; }
@@ -103,6 +113,55 @@ static void batch_launch_as(clb_batch* b, cudaStream_t s) {
     else k_step_batch<P, NPT, false, false><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
 }
 
+// Persistent launch of `nsteps` steps from parity par0.  The grid is as
+// many blocks as can be resident at once (cooperative launch), at most one
+// per tile; the blocks claim the tuned number of tiles at a time.
+template <class P, int NPT>
+static cudaError_t batch_persist_as(clb_batch* b, cudaStream_t s, int par0, int nsteps, int extra,
+                                    long long limit) {
+    using C = CaseT<typename P::R, typename P::S>;
+    using Fn = void (*)(const C*, const int4*, int, int, int, int, GridBarrier*, int, long long);
+    Fn fn = b->shift ? (b->forch ? k_step_batch_persist<P, NPT, true, true> : k_step_batch_persist<P, NPT, true, false>)
+                     : (b->forch ? k_step_batch_persist<P, NPT, false, true> : k_step_batch_persist<P, NPT, false, false>);
+    const dim3 block(kShapes[b->shape][0], kShapes[b->shape][1]);
+    if (b->pgrid == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, (int)(block.x * block.y), 0);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        b->pgrid = std::min(sms * per_sm, std::max(b->ntiles, 1));
+    }
+    const int chunk = b->per_cta;   // tiles claimed at a time (the tuned tiles per block)
+    cudaError_t e = cudaMemsetAsync(b->bar, 0, offsetof(GridBarrier, failed), s);   // arrived, next[]
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)b->pgrid);
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fn, (const C*)b->table, (const int4*)b->tiles, b->ntiles, chunk, par0, nsteps,
+                              b->bar, extra, limit);
+}
+
+// Persistent launch in the batch's precision (coherent loads, see LdCA).
+#ifndef CLB_PERSIST_LD
+#define CLB_PERSIST_LD LdCA
+#endif
+static cudaError_t batch_persist(clb_batch* b, cudaStream_t s, int par0, int nsteps, int extra, long long limit) {
+    using L = CLB_PERSIST_LD;
+    if (b->ntiles == 0) return cudaSuccess;
+    if (b->prec == CLB_F16S) return batch_persist_as<StoreH16T<L>, 2>(b, s, par0, nsteps, extra, limit);
+    if (b->prec == CLB_F16N) return batch_persist_as<StoreH16NT<L>, 2>(b, s, par0, nsteps, extra, limit);
+    return batch_persist_as<StoreF64T<L>, 1>(b, s, par0, nsteps, extra, limit);
+}
+
 static void batch_launch(clb_batch* b, cudaStream_t s) {
     if (b->ntiles > 0) {
         if (b->prec == CLB_F16S) batch_launch_as<StoreH16, 2>(b, s);
@@ -122,7 +181,9 @@ static cudaGraphExec_t batch_capture(clb_batch* b, int par) {
         cudaGetLastError();
         return nullptr;
     }
-    for (int i = 0; i < kGraphSteps; ++i) batch_launch(b, b->cap_stream);
+    if (b->mode == CLB_BATCH_PERSISTENT) batch_persist(b, b->cap_stream, par, kGraphSteps, 0, b->wait_limit);
+    else
+        for (int i = 0; i < kGraphSteps; ++i) batch_launch(b, b->cap_stream);
     const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &gr);
     b->par = save;
     if (e != cudaSuccess || !gr) {
@@ -226,6 +287,11 @@ extern "C" int clb_batch_init(clb_batch** out, int32_t ncase, const clb_params* 
         bfail(b, CLB_ERR_CUDA, "clb_batch_init: case table upload failed");
         return bail(CLB_ERR_CUDA);
     }
+    if (cudaMalloc(&b->bar, sizeof(GridBarrier)) != cudaSuccess ||
+        cudaMemset(b->bar, 0, sizeof(GridBarrier)) != cudaSuccess) {
+        bfail(b, CLB_ERR_CUDA, "clb_batch_init: grid barrier allocation failed");
+        return bail(CLB_ERR_CUDA);
+    }
     const int rc = batch_build_tiles(b);
     if (rc != CLB_OK) return bail(rc);
     *out = b;
@@ -245,8 +311,13 @@ extern "C" int clb_batch_step(clb_batch* b, int64_t n) {
                     continue;
                 }
             }
-            CKB(b, cudaGraphLaunch(b->graph[b->par], b->stream));
+            CKB(b, cudaGraphLaunch(b->graph[b->par], b->stream));   // even count: parity unchanged
             left -= kGraphSteps;
+        } else if (b->mode == CLB_BATCH_PERSISTENT) {
+            const int k = (int)std::min<int64_t>(left, kGraphSteps);
+            CKB(b, batch_persist(b, b->stream, b->par, k, 0, b->wait_limit));
+            b->par ^= k & 1;
+            left -= k;
         } else {
             batch_launch(b, b->stream);
             CKB(b, cudaGetLastError());
@@ -258,6 +329,44 @@ extern "C" int clb_batch_step(clb_batch* b, int64_t n) {
     for (size_t c = 0; c < b->cases.size(); ++c)
         if (b->active[c]) b->cases[c]->t += n;
     return CLB_OK;
+}
+
+// Waits for the batch's stream and reports a grid barrier that gave up
+// (persistent mode) as CLB_ERR_TIMEOUT, clearing the flag.
+static int batch_check(clb_batch* b) {
+    CKB(b, cudaStreamSynchronize(b->stream));
+    if (!b->bar) return CLB_OK;
+    unsigned failed = 0;
+    CKB(b, cudaMemcpy(&failed, &b->bar->failed, sizeof failed, cudaMemcpyDeviceToHost));
+    if (!failed) return CLB_OK;
+    CKB(b, cudaMemset(&b->bar->failed, 0, sizeof failed));
+    return bfail(b, CLB_ERR_TIMEOUT,
+                 "persistent batch: a grid barrier wait expired; the state of the steps since the last check is "
+                 "not valid");
+}
+
+extern "C" int clb_batch_set_mode(clb_batch* b, int32_t mode) {
+    if (!b) return CLB_ERR_ARG;
+    if (mode != CLB_BATCH_GRAPH && mode != CLB_BATCH_PERSISTENT)
+        return bfail(b, CLB_ERR_ARG, "clb_batch_set_mode: mode must be CLB_BATCH_GRAPH or CLB_BATCH_PERSISTENT");
+    const int rc = batch_check(b);
+    if (rc != CLB_OK) return rc;
+    b->mode = mode;
+    batch_drop_graphs(b);
+    return CLB_OK;
+}
+
+extern "C" int clb_batch_barrier_selftest(clb_batch* b, int64_t limit_cycles) {
+    if (!b) return CLB_ERR_ARG;
+    if (limit_cycles < 1 || limit_cycles > 4000000000LL)
+        return bfail(b, CLB_ERR_ARG, "clb_batch_barrier_selftest: limit outside 1 .. 4e9 cycles");
+    int rc = batch_check(b);
+    if (rc != CLB_OK) return rc;
+    // one step whose barrier waits for one block more than the launch has:
+    // the wait must expire; the step wrote only the unused buffer, so the
+    // state (parity, time) stays as it was
+    CKB(b, batch_persist(b, b->stream, b->par, 1, 1, (long long)limit_cycles));
+    return batch_check(b);
 }
 
 extern "C" int clb_batch_set_active(clb_batch* b, const int32_t* active) {
@@ -278,6 +387,8 @@ extern "C" int clb_batch_set_active(clb_batch* b, const int32_t* active) {
 
 extern "C" int clb_batch_nusselt(clb_batch* b, int32_t side, double* nu) {
     if (!b || !nu) return CLB_ERR_ARG;
+    const int rb = batch_check(b);
+    if (rb != CLB_OK) return rb;
     batch_sync_cases(b);
     for (size_t c = 0; c < b->cases.size(); ++c) {
         const int rc = clb_nusselt(b->cases[c], side, &nu[c]);
@@ -288,6 +399,8 @@ extern "C" int clb_batch_nusselt(clb_batch* b, int32_t side, double* nu) {
 
 extern "C" int clb_batch_macros(clb_batch* b, int32_t c, double* rho, double* ux, double* uy, double* T) {
     if (!b || c < 0 || c >= (int32_t)b->cases.size()) return CLB_ERR_ARG;
+    const int rb = batch_check(b);
+    if (rb != CLB_OK) return rb;
     batch_sync_cases(b);
     const int rc = clb_macros(b->cases[c], rho, ux, uy, T);
     if (rc != CLB_OK) return bfail(b, rc, "clb_batch_macros: case %d: %s", c, b->cases[c]->err.c_str());
@@ -348,8 +461,7 @@ extern "C" int64_t clb_batch_time(const clb_batch* b) { return b ? b->t : -1; }
 
 extern "C" int clb_batch_sync(clb_batch* b) {
     if (!b) return CLB_ERR_ARG;
-    CKB(b, cudaStreamSynchronize(b->stream));
-    return CLB_OK;
+    return batch_check(b);
 }
 
 extern "C" const char* clb_batch_last_error(const clb_batch* b) { return b ? b->err.c_str() : g_init_error.c_str(); }
@@ -359,6 +471,7 @@ extern "C" void clb_batch_destroy(clb_batch* b) {
     cudaStreamSynchronize(b->stream);
     batch_drop_graphs(b);
     for (clb_handle* h : b->cases) clb_destroy(h);
+    cudaFree(b->bar);
     cudaFree(b->table);
     cudaFree(b->tiles);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);

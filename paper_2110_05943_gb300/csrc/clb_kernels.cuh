@@ -102,6 +102,7 @@ struct KParamsT {
     R T0;         // reference temperature (baseline record of the FP16N form)
     R wf[9];      // rest-state offsets of the stored distributions (FP16 form)
     R wg[5];
+    R wfs[9];     // wf * 2^12 (the stored scale)
 };
 
 // Pointers that are not distributions: per-node constants (FP64 form),
@@ -135,15 +136,19 @@ __host__ __device__ inline BufT<const S> as_const(const BufT<S>& b) {
 // The FP16 forms store their values with unbiased stochastic rounding:
 // round-to-nearest of a value that depends on the state is a systematic
 // error that the time march accumulates (it acts as a steady heat source),
-// whereas randomised rounding leaves zero-mean noise.  Six random bits per
-// value are added below the 10 kept mantissa bits (13 bits are discarded
-// between FP32 and FP16) together with half of the remaining 2^7, then the
-// value is truncated towards zero; the expected stored value equals the FP32
-// value to 1/128 of an FP16 unit in the last place (in FP16's normal range).
-// The bits come from the 32-bit integer mixer "lowbias32" (C. Wellons'
+// whereas randomised rounding leaves zero-mean noise.  sm_100-family GPUs
+// round stochastically in hardware: cvt.rs.f16x2.f32 adds 13 random bits
+// below the 10 kept mantissa bits (the 13 that FP32 -> FP16 drops) and
+// truncates, so a value is rounded away from zero with probability equal
+// to its dropped fraction -- the expected stored value equals the FP32
+// value exactly.  Its first source goes to the upper half and draws on bits
+// 16..28 of the random word, the second on bits 0..12 (checked on the GPU).
+// The words come from the 32-bit integer mixer "lowbias32" (C. Wellons'
 // hash-prospector) keyed by the node's plane offset and the buffer's step
-// counter, stretched to three words by xorshift-multiply rounds, so runs
-// stay deterministic and bit-reproducible.
+// counter: h0 = mix(node, step), h1 = an odd multiple of a second mix, and
+// value k of a node (pair) uses h0 + k h1 (a Weyl sequence: every word,
+// and each 13-bit field of it, is uniform).  Runs stay deterministic and
+// bit-reproducible.
 CLB_HD uint32_t mix32(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352dU;
@@ -154,38 +159,31 @@ CLB_HD uint32_t mix32(uint32_t x) {
 }
 
 struct Dither {
-    uint32_t h[3];   // 15 six-bit fields: values 0-8 (f), 9-13 (g)
+    uint32_t h0, h1;   // value k uses the word h0 + k h1
 };
 
 CLB_HD Dither dither_for(uint32_t node, uint32_t seq) {
     Dither d;
-    d.h[0] = mix32(node * 0x9E3779B1U ^ mix32(seq + 0x632BE5ABU));
-    // two more words by one xorshift-multiply round each (h[0] is already mixed)
-    d.h[1] = (d.h[0] ^ (d.h[0] >> 15)) * 0x85EBCA77U;
-    d.h[2] = (d.h[1] ^ (d.h[1] >> 13)) * 0xC2B2AE3DU;
+    d.h0 = mix32(node * 0x9E3779B1U ^ mix32(seq + 0x632BE5ABU));
+    d.h1 = ((d.h0 ^ (d.h0 >> 15)) * 0x85EBCA77U) | 1U;
     return d;
 }
 
-CLB_HD uint32_t dbits(const Dither& d, int i) { return (d.h[i / 5] >> (6 * (i % 5))) & 63U; }
+CLB_HD uint32_t dword(const Dither& d, int k) { return d.h0 + (uint32_t)k * d.h1; }
 
-CLB_HD __half sr_half(float v, uint32_t r6) {
-    return __float2half_rz(__uint_as_float(__float_as_uint(v) + ((r6 << 7) | 0x40U)));
+// lo -> .x (bits 0..15), hi -> .y, stochastically rounded with the random word r.
+CLB_HD __half2 sr_half2(float lo, float hi, uint32_t r) {
+    uint32_t v;
+    asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(v) : "f"(hi), "f"(lo), "r"(r));
+    return *reinterpret_cast<const __half2*>(&v);
 }
 
-// The same for a node pair in one packed conversion: lo -> .x, hi -> .y
-// (cvt.rz.f16x2.f32 puts its first source in the upper half).
-CLB_HD __half2 sr_half2(float lo, uint32_t rlo, float hi, uint32_t rhi) {
-    const float a = __uint_as_float(__float_as_uint(hi) + ((rhi << 7) | 0x40U));
-    const float b = __uint_as_float(__float_as_uint(lo) + ((rlo << 7) | 0x40U));
-    uint32_t r;
-    asm("cvt.rz.f16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(a), "f"(b));
-    return *reinterpret_cast<const __half2*>(&r);
-}
+CLB_HD __half sr_half(float v, uint32_t r) { return __low2half(sr_half2(v, 0.0f, r)); }
 
 // Stored FP16 values are the deviations times 2^12 (exact): most
 // deviations of the equilibrium-shifted form lie below FP16's smallest
-// normal number (6.1e-5), where FP16 has a fixed spacing and the dithered
-// rounding above would truncate; scaled, everything above 1.5e-8 is normal.
+// normal number (6.1e-5), where FP16 has a fixed absolute spacing;
+// scaled, everything above 1.5e-8 keeps FP16's full relative precision.
 // The largest storable deviation is 16.
 constexpr float kDevScale = 4096.0f, kDevInv = 1.0f / 4096.0f;
 
@@ -629,10 +627,47 @@ __device__ __forceinline__ PhysT<f2> splat(const PhysT<float>& p) {
 __device__ __forceinline__ constexpr bool column_dir(int i) { return i == 0 || i == 2 || i == 4; }
 
 // ---------------------------------------------------------------- storage
+// Loads of the distribution buffers.  A kernel that only reads its input
+// buffer takes the read-only (non-coherent) cache path.  The persistent
+// batch kernel reads, in one step, what other blocks wrote in the step
+// before, which the read-only path does not allow; it uses ordinary
+// (coherent) loads, L2-only ones (LdCG) or L1-cached ones (LdCA), made
+// consistent by the acquire fence after its grid barrier.
+struct LdNC {
+    template <class T>
+    static __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+    static __device__ __forceinline__ double ld_again(const double* p) {
+        double v;
+        asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
+};
+struct LdCG {
+    template <class T>
+    static __device__ __forceinline__ T ld(const T* p) { return __ldcg(p); }
+    static __device__ __forceinline__ double ld_again(const double* p) {
+        double v;
+        asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
+};
+
+struct LdCA {
+    template <class T>
+    static __device__ __forceinline__ T ld(const T* p) { return *p; }
+    static __device__ __forceinline__ double ld_again(const double* p) {
+        double v;
+        asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+        return v;
+    }
+};
+
 // A storage policy reads the streamed values of a node (pull9 / pull5),
 // writes a node's post-collision values (store) and gives the per-node
-// constants (coef).
-struct StoreF64 {
+// constants (coef).  L: how the distribution buffers are loaded.
+template <class L>
+struct StoreF64T {
+    using Ld = L;
     static constexpr bool kCentred = false;   // g and T carried as they are
     static constexpr bool kReload = true;     // interior f re-read before the update (see step_node)
     using R = double;
@@ -642,14 +677,14 @@ struct StoreF64 {
         long long o[9];
         sources<long long>(K.g, x, y, o);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = __ldg(B.f + i * K.g.plane + o[i]);
+        for (int i = 0; i < 9; ++i) f[i] = L::ld(B.f + i * K.g.plane + o[i]);
     }
     static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
                                                  int y, R (&g)[5]) {
         long long o[9];
         sources<long long>(K.g, x, y, o);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = __ldg(B.g + i * K.g.plane + o[i]);
+        for (int i = 0; i < 5; ++i) g[i] = L::ld(B.g + i * K.g.plane + o[i]);
     }
     static __device__ __forceinline__ void pull(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
                                                 int y, R (&f)[9], R (&g)[5]) {
@@ -663,8 +698,7 @@ struct StoreF64 {
         long long o[9];
         sources<long long>(K.g, x, y, o);
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(f[i]) : "l"(B.f + i * K.g.plane + o[i]));
+        for (int i = 0; i < 9; ++i) f[i] = L::ld_again(B.f + i * K.g.plane + o[i]);
     }
     static __device__ __forceinline__ void store(const BufT<S>& B, const KParamsT<R>& K, int x, int y,
                                                  const R (&f)[9], const R (&g)[5], R, R, R, R, R, uint32_t) {
@@ -679,6 +713,8 @@ struct StoreF64 {
         return A.coef[(long long)y * K.g.nx + x];
     }
 };
+
+using StoreF64 = StoreF64T<LdNC>;
 
 // FP32 constants of a node from its porosity and its row's a_y - g beta T0
 // (Eqs. 4, 5, 23).
@@ -698,7 +734,9 @@ __device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, float a
     return c;
 }
 
-struct StoreH16 {
+template <class L>
+struct StoreH16T {
+    using Ld = L;
     // g is carried rest-centred (g - g_rest(T0), T - T0): the stored
     // deviations are exactly that, so no baseline is added or subtracted
     static constexpr bool kCentred = true;
@@ -711,7 +749,7 @@ struct StoreH16 {
         sources<int>(K.g, x, y, o);
         const int Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = fma(__half2float(__ldg(B.f + i * Q + o[i])), kDevInv, K.wf[i]);
+        for (int i = 0; i < 9; ++i) f[i] = fma(__half2float(L::ld(B.f + i * Q + o[i])), kDevInv, K.wf[i]);
     }
     static __device__ __forceinline__ void pull5(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
                                                  int y, R (&g)[5]) {
@@ -719,7 +757,7 @@ struct StoreH16 {
         sources<int>(K.g, x, y, o);
         const int Q = (int)K.g.plane;
 #pragma unroll
-        for (int i = 0; i < 5; ++i) g[i] = __half2float(__ldg(B.g + i * Q + o[i])) * kDevInv;
+        for (int i = 0; i < 5; ++i) g[i] = __half2float(L::ld(B.g + i * Q + o[i])) * kDevInv;
     }
     static __device__ __forceinline__ void pull(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
                                                 int y, R (&f)[9], R (&g)[5]) {
@@ -731,34 +769,36 @@ struct StoreH16 {
         const int o = y * K.g.px + x, Q = (int)K.g.plane;
         const Dither d = dither_for((uint32_t)o, seq);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - K.wf[i]) * kDevScale, dbits(d, i));
+        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - K.wf[i]) * kDevScale, dword(d, i));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half(g[i] * kDevScale, dbits(d, 9 + i));
+        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half(g[i] * kDevScale, dword(d, 9 + i));
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
         const float p = __ldg(A.phi + y * K.g.nx + x);
         return coef_from_phi<FORCH>(p, recip(p), A.ayg[y], K);
     }
-    // Two interior nodes (x0, x0 + 1), x0 even.
+    // Two interior nodes (x0, x0 + 1), x0 even, neither at the periodic x
+    // seam: node x0 + 1 pulls from the offsets of node x0 plus one.
     static __device__ __forceinline__ void pull2(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x0,
                                                  int y, f2 (&f)[9], f2 (&g)[5]) {
-        int o0[9], o1[9];
-        sources<int>(K.g, x0, y, o0);
-        sources<int>(K.g, x0 + 1, y, o1);
+        int o[9];
+        sources<int>(K.g, x0, y, o);
         const int Q = (int)K.g.plane;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
+            const __half* p = B.f + i * Q + o[i];
             float2 v;
-            if (column_dir(i)) v = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.f + i * Q + o0[i])));
-            else v = make_float2(__half2float(__ldg(B.f + i * Q + o0[i])), __half2float(__ldg(B.f + i * Q + o1[i])));
+            if (column_dir(i)) v = __half22float2(L::ld(reinterpret_cast<const __half2*>(p)));
+            else v = make_float2(__half2float(L::ld(p)), __half2float(L::ld(p + 1)));
             f[i] = fma(f2::make(v.x, v.y), f2(kDevInv), f2(K.wf[i]));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
+            const __half* p = B.g + i * Q + o[i];
             float2 v;
-            if (column_dir(i)) v = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.g + i * Q + o0[i])));
-            else v = make_float2(__half2float(__ldg(B.g + i * Q + o0[i])), __half2float(__ldg(B.g + i * Q + o1[i])));
+            if (column_dir(i)) v = __half22float2(L::ld(reinterpret_cast<const __half2*>(p)));
+            else v = make_float2(__half2float(L::ld(p)), __half2float(L::ld(p + 1)));
             g[i] = f2::make(v.x, v.y) * f2(kDevInv);
         }
     }
@@ -766,30 +806,31 @@ struct StoreH16 {
                                                   const f2 (&f)[9], const f2 (&g)[5], f2, f2, f2, f2, f2,
                                                   uint32_t seq) {
         const int o = y * K.g.px + x0, Q = (int)K.g.plane;
-        const Dither d0 = dither_for((uint32_t)o, seq), d1 = dither_for((uint32_t)o + 1U, seq);
+        const Dither rw = dither_for((uint32_t)o, seq);   // one word per stored pair
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const f2 d = (f[i] - f2(K.wf[i])) * f2(kDevScale);
-            *reinterpret_cast<__half2*>(B.f + i * Q + o) =
-                sr_half2(d.lo(), dbits(d0, i), d.hi(), dbits(d1, i));
+            const f2 d = fma(f[i], f2(kDevScale), f2(-K.wfs[i]));   // (f - w_i rho_0) 2^12
+            *reinterpret_cast<__half2*>(B.f + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, i));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const f2 d = g[i] * f2(kDevScale);
-            *reinterpret_cast<__half2*>(B.g + i * Q + o) =
-                sr_half2(d.lo(), dbits(d0, 9 + i), d.hi(), dbits(d1, 9 + i));
+            *reinterpret_cast<__half2*>(B.g + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, 9 + i));
         }
     }
 };
+
+using StoreH16 = StoreH16T<LdNC>;
 
 // Baseline (rho, u, T - T0, 1/phi) of the node whose record sits at plane offset o.
 struct Base {
     float rho, X, Y, Tt, ip;
 };
 
+template <class L>
 __device__ __forceinline__ Base load_base(const BufT<const __half>& B, const AuxT<float>& A,
                                           const KParamsT<float>& K, int o) {
-    const uint2 r = __ldg(B.rec + o);
+    const uint2 r = L::ld(B.rec + o);
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&r.x));
     const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&r.y));
     Base s;
@@ -826,18 +867,20 @@ __device__ __forceinline__ R feq_comp(R rho, R X, R Y, R ip) {
     return R(0.25) * (fma(rho, fma(R(1.0 / 3.0), fma(R(sx), X, R(sy) * Y), R(1.0 / 9.0)), fma(A, t, Q)));
 }
 
-template <int I>
+template <int I, class L>
 __device__ __forceinline__ void pull_one(const BufT<const __half>& B, const AuxT<float>& A, const KParamsT<float>& K,
                                          const int (&o)[9], float (&f)[9], float (&g)[5], bool want_f, bool want_g) {
-    const Base s = load_base(B, A, K, o[I]);
+    const Base s = load_base<L>(B, A, K, o[I]);
     const int Q = (int)K.g.plane;
-    if (want_f) f[I] = fma(__half2float(__ldg(B.f + I * Q + o[I])), kDevInv, feq_comp<I>(s.rho, s.X, s.Y, s.ip));
+    if (want_f) f[I] = fma(__half2float(L::ld(B.f + I * Q + o[I])), kDevInv, feq_comp<I>(s.rho, s.X, s.Y, s.ip));
     if (I < 5 && want_g)
-        g[I < 5 ? I : 0] = fma(__half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o[I])), kDevInv,
+        g[I < 5 ? I : 0] = fma(__half2float(L::ld(B.g + (I < 5 ? I : 0) * Q + o[I])), kDevInv,
                                geqc_comp<(I < 5 ? I : 0)>(s.Tt, s.X, s.Y, K.p.sigma, K.p.cT2, K.T0));
 }
 
-struct StoreH16N {
+template <class L>
+struct StoreH16NT {
+    using Ld = L;
     static constexpr bool kCentred = true;    // g - g_rest(T0) and T - T0 (see geqc_comp)
     static constexpr bool kReload = false;
     using R = float;
@@ -846,15 +889,15 @@ struct StoreH16N {
                                                     int x, int y, R (&f)[9], R (&g)[5], bool wf, bool wg) {
         int o[9];
         sources<int>(K.g, x, y, o);
-        pull_one<0>(B, A, K, o, f, g, wf, wg);
-        pull_one<1>(B, A, K, o, f, g, wf, wg);
-        pull_one<2>(B, A, K, o, f, g, wf, wg);
-        pull_one<3>(B, A, K, o, f, g, wf, wg);
-        pull_one<4>(B, A, K, o, f, g, wf, wg);
-        pull_one<5>(B, A, K, o, f, g, wf, wg);
-        pull_one<6>(B, A, K, o, f, g, wf, wg);
-        pull_one<7>(B, A, K, o, f, g, wf, wg);
-        pull_one<8>(B, A, K, o, f, g, wf, wg);
+        pull_one<0, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<1, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<2, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<3, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<4, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<5, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<6, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<7, L>(B, A, K, o, f, g, wf, wg);
+        pull_one<8, L>(B, A, K, o, f, g, wf, wg);
     }
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x,
                                                  int y, R (&f)[9]) {
@@ -895,37 +938,38 @@ struct StoreH16N {
                              geqc_comp<4>(bT, bX, bY, s, c, t0)};
         const Dither d = dither_for((uint32_t)o, seq);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - fe[i]) * kDevScale, dbits(d, i));
+        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - fe[i]) * kDevScale, dword(d, i));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half((g[i] - ge[i]) * kDevScale, dbits(d, 9 + i));
+        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half((g[i] - ge[i]) * kDevScale, dword(d, 9 + i));
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
         const float ip = __ldg(A.ip + y * K.g.px + x);
         return coef_from_phi<FORCH>(recip(ip), ip, A.ayg[y], K);
     }
-    // Two interior nodes (x0, x0 + 1), x0 even.
+    // Two interior nodes (x0, x0 + 1), x0 even, neither at the periodic x
+    // seam (node x0 + 1 pulls from node x0's offsets plus one).
     template <int I>
     static __device__ __forceinline__ void pull2_one(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K,
-                                                     const int (&o0)[9], const int (&o1)[9], f2 (&f)[9], f2 (&g)[5]) {
+                                                     const int (&o0)[9], f2 (&f)[9], f2 (&g)[5]) {
         const int Q = (int)K.g.plane;
         uint2 r0, r1;
         float2 ip, df, dg = make_float2(0.0f, 0.0f);
         if (column_dir(I)) {
-            const uint4 r = __ldg(reinterpret_cast<const uint4*>(B.rec + o0[I]));
+            const uint4 r = L::ld(reinterpret_cast<const uint4*>(B.rec + o0[I]));
             r0 = make_uint2(r.x, r.y);
             r1 = make_uint2(r.z, r.w);
             ip = __ldg(reinterpret_cast<const float2*>(A.ip + o0[I]));
-            df = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.f + I * Q + o0[I])));
-            if (I < 5) dg = __half22float2(__ldg(reinterpret_cast<const __half2*>(B.g + (I < 5 ? I : 0) * Q + o0[I])));
+            df = __half22float2(L::ld(reinterpret_cast<const __half2*>(B.f + I * Q + o0[I])));
+            if (I < 5) dg = __half22float2(L::ld(reinterpret_cast<const __half2*>(B.g + (I < 5 ? I : 0) * Q + o0[I])));
         } else {
-            r0 = __ldg(B.rec + o0[I]);
-            r1 = __ldg(B.rec + o1[I]);
-            ip = make_float2(__ldg(A.ip + o0[I]), __ldg(A.ip + o1[I]));
-            df = make_float2(__half2float(__ldg(B.f + I * Q + o0[I])), __half2float(__ldg(B.f + I * Q + o1[I])));
+            r0 = L::ld(B.rec + o0[I]);
+            r1 = L::ld(B.rec + o0[I] + 1);
+            ip = make_float2(__ldg(A.ip + o0[I]), __ldg(A.ip + o0[I] + 1));
+            df = make_float2(__half2float(L::ld(B.f + I * Q + o0[I])), __half2float(L::ld(B.f + I * Q + o0[I] + 1)));
             if (I < 5)
-                dg = make_float2(__half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o0[I])),
-                                 __half2float(__ldg(B.g + (I < 5 ? I : 0) * Q + o1[I])));
+                dg = make_float2(__half2float(L::ld(B.g + (I < 5 ? I : 0) * Q + o0[I])),
+                                 __half2float(L::ld(B.g + (I < 5 ? I : 0) * Q + o0[I] + 1)));
         }
         const float2 a0 = __half22float2(*reinterpret_cast<const __half2*>(&r0.x));
         const float2 b0 = __half22float2(*reinterpret_cast<const __half2*>(&r0.y));
@@ -942,18 +986,17 @@ struct StoreH16N {
     }
     static __device__ __forceinline__ void pull2(const BufT<const S>& B, const AuxT<R>& A, const KParamsT<R>& K, int x0,
                                                  int y, f2 (&f)[9], f2 (&g)[5]) {
-        int o0[9], o1[9];
+        int o0[9];                                   // node x0 + 1: the same offsets plus one
         sources<int>(K.g, x0, y, o0);
-        sources<int>(K.g, x0 + 1, y, o1);
-        pull2_one<0>(B, A, K, o0, o1, f, g);
-        pull2_one<1>(B, A, K, o0, o1, f, g);
-        pull2_one<2>(B, A, K, o0, o1, f, g);
-        pull2_one<3>(B, A, K, o0, o1, f, g);
-        pull2_one<4>(B, A, K, o0, o1, f, g);
-        pull2_one<5>(B, A, K, o0, o1, f, g);
-        pull2_one<6>(B, A, K, o0, o1, f, g);
-        pull2_one<7>(B, A, K, o0, o1, f, g);
-        pull2_one<8>(B, A, K, o0, o1, f, g);
+        pull2_one<0>(B, A, K, o0, f, g);
+        pull2_one<1>(B, A, K, o0, f, g);
+        pull2_one<2>(B, A, K, o0, f, g);
+        pull2_one<3>(B, A, K, o0, f, g);
+        pull2_one<4>(B, A, K, o0, f, g);
+        pull2_one<5>(B, A, K, o0, f, g);
+        pull2_one<6>(B, A, K, o0, f, g);
+        pull2_one<7>(B, A, K, o0, f, g);
+        pull2_one<8>(B, A, K, o0, f, g);
     }
     static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
                                                   const f2 (&f)[9], const f2 (&g)[5], f2 rho, f2 X, f2 Y, f2 T, f2 ip,
@@ -979,21 +1022,21 @@ struct StoreH16N {
         const f2 ge[5] = {geqc_comp<0>(bT, bX, bY, s, c, t0), geqc_comp<1>(bT, bX, bY, s, c, t0),
                           geqc_comp<2>(bT, bX, bY, s, c, t0), geqc_comp<3>(bT, bX, bY, s, c, t0),
                           geqc_comp<4>(bT, bX, bY, s, c, t0)};
-        const Dither d0 = dither_for((uint32_t)o, seq), d1 = dither_for((uint32_t)o + 1U, seq);
+        const Dither rw = dither_for((uint32_t)o, seq);   // one word per stored pair
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const f2 d = (f[i] - fe[i]) * f2(kDevScale);
-            *reinterpret_cast<__half2*>(B.f + i * Q + o) =
-                sr_half2(d.lo(), dbits(d0, i), d.hi(), dbits(d1, i));
+            *reinterpret_cast<__half2*>(B.f + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, i));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const f2 d = (g[i] - ge[i]) * f2(kDevScale);
-            *reinterpret_cast<__half2*>(B.g + i * Q + o) =
-                sr_half2(d.lo(), dbits(d0, 9 + i), d.hi(), dbits(d1, 9 + i));
+            *reinterpret_cast<__half2*>(B.g + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, 9 + i));
         }
     }
 };
+
+using StoreH16N = StoreH16NT<LdNC>;
 
 // Inward normal of a wall node and the sides that set its velocity and
 // temperature.  Returns false for an interior node.
@@ -1115,10 +1158,10 @@ __device__ __forceinline__ void node_state(const BufT<const typename P::S>& Bin,
 // Step counter of the input buffer (FP16 forms; 0 without one); the thread
 // of node (0, 0) writes the next value into the output buffer, which no
 // thread of this launch reads.
-template <typename S>
+template <class L, typename S>
 __device__ __forceinline__ uint32_t step_seq(const BufT<S>& in, const BufT<S>& out, int x, int y) {
     if (!in.seq) return 0U;
-    const uint32_t seq = *in.seq;
+    const uint32_t seq = L::ld(in.seq);
     if (x == 0 && y == 0) *out.seq = seq + 1U;
     return seq;
 }
@@ -1134,7 +1177,7 @@ __device__ __forceinline__ void step_interior(const BufT<typename P::S>& in, con
                                               int x, int y) {
     using R = typename P::R;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
-    const uint32_t seq = step_seq(in, out, x, y);
+    const uint32_t seq = step_seq<typename P::Ld>(in, out, x, y);
     R f[9], g[5];
     P::pull(as_const(in), A, K, x, y, f, g);
     const Mom9T<R> k = moments9(f);
@@ -1158,7 +1201,7 @@ __device__ __forceinline__ void step_wall(const BufT<typename P::S>& in, const B
                                           int y, const WallInfo& w) {
     using R = typename P::R;
     const CoefT<R> c = P::template coef<FORCH>(A, K, x, y);
-    const uint32_t seq = step_seq(in, out, x, y);
+    const uint32_t seq = step_seq<typename P::Ld>(in, out, x, y);
     R f[9], g[5];
     R rho, X, Y, T, Tt, hFx, hFy, n0;
     wall_state<P, FORCH>(as_const(in), A, K, x, y, w, c, f, g, rho, X, Y, T, Tt, n0);
@@ -1245,19 +1288,13 @@ __global__ void __launch_bounds__(CLB_F64_THREADS, CLB_F64_MINB)
 }
 
 // FP16 forms, two nodes (x0, x0 + 1) per thread: interior pairs run the
-// collision on packed FP32 pairs; a pair with a wall node (or the odd last
-// column) falls back to the per-node path.  128-thread blocks capped at
-// 96 registers: 5 resident blocks (20 warps) per SM, no spills.
+// collision on packed FP32 pairs.  A pair that touches a wall, the first
+// and the last pair of a row (at a periodic x seam node x0 + 1 would not
+// pull from node x0's offsets plus one) and the odd last column fall back
+// to the per-node path.
 template <class P, bool SHIFT, bool FORCH>
-__device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
-                                          const AuxT<float>& A, const KParamsT<float>& K, int x0, int y) {
-    const bool has1 = x0 + 1 < K.g.nx;
-    WallInfo w;
-    if (!has1 || wall_info(K.g, K.b, x0, y, w) || wall_info(K.g, K.b, x0 + 1, y, w)) {
-        step_node<P, SHIFT, FORCH>(in, out, A, K, x0, y);
-        if (has1) step_node<P, SHIFT, FORCH>(in, out, A, K, x0 + 1, y);
-        return;
-    }
+__device__ __forceinline__ void step_pair_interior(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
+                                                   const AuxT<float>& A, const KParamsT<float>& K, int x0, int y) {
     const PhysT<f2> P2 = splat(K.p);
     const CoefT<f2> c = pack_coef(P::template coef<FORCH>(A, K, x0, y), P::template coef<FORCH>(A, K, x0 + 1, y));
     f2 f[9], g[5];
@@ -1272,16 +1309,93 @@ __device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const B
     collide9<f2, SHIFT>(f, k, k.rho, X, Y, hFx, hFy, c.ip, P2);
     if constexpr (P::kCentred) collide5_centred<f2, SHIFT>(g, n0, Tt, X, Y, f2(K.T0), P2);
     else collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
-    P::store2(out, K, x0, y, f, g, k.rho, X, Y, Tt, c.ip, step_seq(in, out, x0, y));
+    P::store2(out, K, x0, y, f, g, k.rho, X, Y, Tt, c.ip, step_seq<typename P::Ld>(in, out, x0, y));
+}
+
+// True if the pair (x0, x0 + 1) takes the packed path.
+__device__ __forceinline__ bool interior_pair(const Geo& G, int x0, int y) {
+    return x0 > 0 && x0 + 2 < G.nx && !(G.wall_y && (y == 0 || y == G.ny - 1));
 }
 
 template <class P, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(128, 5) k_step2(const BufT<typename P::S> in, const BufT<typename P::S> out,
-                                                  const AuxT<float> A, const KParamsT<float> K) {
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= K.g.nx || y >= K.g.ny) return;
-    step_pair<P, SHIFT, FORCH>(in, out, A, K, x0, y);
+__device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
+                                          const AuxT<float>& A, const KParamsT<float>& K, int x0, int y) {
+    if (interior_pair(K.g, x0, y)) {
+        step_pair_interior<P, SHIFT, FORCH>(in, out, A, K, x0, y);
+    } else {
+        step_node<P, SHIFT, FORCH>(in, out, A, K, x0, y);
+        if (x0 + 1 < K.g.nx) step_node<P, SHIFT, FORCH>(in, out, A, K, x0 + 1, y);
+    }
+}
+
+// Nodes that the per-node path takes in k_step2 ("edge" nodes): all nodes
+// of walled S/N rows, and in every other row the nodes of its first and its
+// last pair (all nodes of a row with fewer than three pairs).  Count and
+// the i-th one.
+__host__ __device__ inline int edge_per_row(int nx) {
+    const int np = (nx + 1) / 2;
+    if (np < 3) return nx;
+    const int xl = 2 * (np - 1);
+    return 2 + (nx - xl);   // {0, 1} and {xl, xl + 1} within the row
+}
+
+__host__ __device__ inline long long edge_count(const Geo& G) {
+    const int rows = G.wall_y ? G.ny - 2 : G.ny;
+    return (G.wall_y ? 2LL * G.nx : 0LL) + (long long)rows * edge_per_row(G.nx);
+}
+
+__device__ __forceinline__ void edge_node(const Geo& G, long long i, int& x, int& y) {
+    if (G.wall_y) {
+        if (i < G.nx) { x = (int)i; y = 0; return; }
+        if (i < 2LL * G.nx) { x = (int)(i - G.nx); y = G.ny - 1; return; }
+        i -= 2LL * G.nx;
+    }
+    const int ne = edge_per_row(G.nx);
+    const int r = (int)(i / ne), k = (int)(i - (long long)r * ne);
+    y = r + (G.wall_y ? 1 : 0);
+    const int np = (G.nx + 1) / 2;
+    x = (np < 3 || k < 2) ? k : 2 * (np - 1) + (k - 2);
+}
+
+// One launch, two kinds of blocks (no warp mixes the packed and the
+// per-node path): blocks [0, n_tiles) cover all pairs of the grid in
+// tiles_x x ... tiles of blockDim pairs, aligned at x = 0 so that a warp's
+// 64 nodes are one 128-byte line of every FP16 plane, and skip the pairs
+// that are not interior; the blocks after them take the edge nodes, one per
+// thread, with 128-thread blocks.
+// Resident 128-thread blocks per SM the registers of k_step2 are capped
+// for, per form (measured at 8192^2): the rest-shifted form fits 6 (<= 80
+// registers, 24 warps: 77.1 GLUPS against 74.7 with 5); the
+// equilibrium-shifted form spills below 96 registers (6 blocks: 38.1
+// GLUPS, 5 blocks: 45.9).
+template <class P>
+struct Step2MinBlocks {
+    static constexpr int value = 5;
+};
+template <class L>
+struct Step2MinBlocks<StoreH16T<L>> {
+    static constexpr int value = 6;
+};
+
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, Step2MinBlocks<P>::value)
+    k_step2(const BufT<typename P::S> in, const BufT<typename P::S> out,
+                                                  const AuxT<float> A, const KParamsT<float> K, int tiles_x,
+                                                  int n_tiles) {
+    const int b = blockIdx.x;
+    if (b < n_tiles) {
+        const int x0 = 2 * ((b % tiles_x) * blockDim.x + threadIdx.x);
+        const int y = (b / tiles_x) * blockDim.y + threadIdx.y;
+        if (y >= K.g.ny || !interior_pair(K.g, x0, y)) return;
+        step_pair_interior<P, SHIFT, FORCH>(in, out, A, K, x0, y);
+    } else {
+        const long long i = (long long)(b - n_tiles) * (blockDim.x * blockDim.y) + threadIdx.y * blockDim.x +
+                            threadIdx.x;
+        if (i >= edge_count(K.g)) return;
+        int x, y;
+        edge_node(K.g, i, x, y);
+        step_node<P, SHIFT, FORCH>(in, out, A, K, x, y);
+    }
 }
 
 // ---------------------------------------------------------------- batches
@@ -1295,22 +1409,18 @@ struct CaseT {
     int pad_;
 };
 
-// Independent cases advanced by one launch.  `tiles` lists (case, x0, y0)
-// in case order; CTA b owns the contiguous range [b * per_cta, ...), and its
-// threads cover a (NPT * blockDim.x) x blockDim.y block of nodes at each
-// tile (NPT = nodes per thread: 2 for the FP16 forms, 1 for FP64).  The
-// case descriptor is staged in shared memory whenever the case changes.
+// Independent cases advanced together.  `tiles` lists (case, x0, y0) in
+// case order; a block takes the contiguous range [t0, t1), and its threads
+// cover a (NPT * blockDim.x) x blockDim.y block of nodes at each tile (NPT =
+// nodes per thread: 2 for the FP16 forms, 1 for FP64).  The case descriptor
+// is staged in shared memory (raw) whenever the case changes.
 template <class P, int NPT, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(128, 4) k_step_batch(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
-                                                       const int4* __restrict__ tiles, int ntiles, int per_cta,
-                                                       int par) {
+__device__ __forceinline__ void batch_tiles(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
+                                            const int4* __restrict__ tiles, int t0, int t1, int par,
+                                            unsigned char* raw, int& cur) {
     using C = CaseT<typename P::R, typename P::S>;
-    __shared__ __align__(16) unsigned char raw[sizeof(C)];
     C& sc = *reinterpret_cast<C*>(raw);
-    const int t0 = blockIdx.x * per_cta;
-    const int t1 = min(t0 + per_cta, ntiles);
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
-    int cur = -1;
     for (int t = t0; t < t1; ++t) {
         const int4 tl = __ldg(tiles + t);
         if (tl.x != cur) {
@@ -1328,6 +1438,95 @@ __global__ void __launch_bounds__(128, 4) k_step_batch(const CaseT<typename P::R
             else
                 step_node<P, SHIFT, FORCH>(sc.b[par ^ sc.flip], sc.b[1 - (par ^ sc.flip)], sc.A, sc.K, x, y);
         }
+    }
+}
+
+// One step per launch: block b owns tiles [b * per_cta, (b + 1) * per_cta).
+template <class P, int NPT, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, 4) k_step_batch(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
+                                                       const int4* __restrict__ tiles, int ntiles, int per_cta,
+                                                       int par) {
+    __shared__ __align__(16) unsigned char raw[sizeof(CaseT<typename P::R, typename P::S>)];
+    const int t0 = blockIdx.x * per_cta;
+    int cur = -1;
+    batch_tiles<P, NPT, SHIFT, FORCH>(cases, tiles, t0, min(t0 + per_cta, ntiles), par, raw, cur);
+}
+
+// Grid barrier and work counters of the persistent batch launch, in device
+// memory.  `arrived` counts block arrivals and next[s & 1] hands out the
+// tiles of step s (both cleared before every launch; next[(s + 1) & 1] is
+// cleared again by block 0 during step s, before it arrives); `failed` is
+// set by a block whose wait gave up and stays set until the host reads and
+// clears it.
+struct GridBarrier {
+    unsigned arrived;
+    unsigned next[2];
+    unsigned failed;
+};
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Block-wide: all blocks of the launch (plus `extra` that do not exist, for
+// the failure-path test) arrive for step `step`; false if the wait gave up
+// after `limit` SM clock cycles or another block had given up.  The
+// __threadfence before arriving publishes this block's stores of the step,
+// the acquiring load and the fence after the wait make the other blocks'
+// stores visible (loads of the next step go to L2: LdCG).
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, int step, int extra, long long limit, int* s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        atomicAdd(&bar->arrived, 1u);
+        const unsigned target = (unsigned)(step + 1) * (unsigned)(gridDim.x + extra);
+        int ok = 1;
+        const long long t0 = clock64();
+        while (ld_acquire_gpu(&bar->arrived) < target) {
+            if (ld_acquire_gpu(&bar->failed)) { ok = 0; break; }
+            if (clock64() - t0 > limit) {
+                atomicExch(&bar->failed, 1u);
+                ok = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// Persistent form: one cooperative launch (every block resident) advances
+// the batch `nsteps` steps.  Within a step the blocks claim `chunk` tiles
+// at a time from a counter (the tiles cost unequal amounts: wall tiles,
+// ragged edges), and a bounded grid barrier separates the steps.  A barrier
+// that gives up sets bar->failed and every block returns; the host reports
+// CLB_ERR_TIMEOUT.
+template <class P, int NPT, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, 4)
+    k_step_batch_persist(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
+                         const int4* __restrict__ tiles, int ntiles, int chunk, int par0, int nsteps,
+                         GridBarrier* bar, int extra, long long limit) {
+    __shared__ __align__(16) unsigned char raw[sizeof(CaseT<typename P::R, typename P::S>)];
+    __shared__ int s_ok, s_t;
+    const bool lead = threadIdx.x == 0 && threadIdx.y == 0;
+    int cur = -1;
+    for (int step = 0; step < nsteps; ++step) {
+        if (lead && blockIdx.x == 0) bar->next[(step + 1) & 1] = 0u;   // published by the barrier below
+        while (true) {
+            if (lead) s_t = (int)atomicAdd(&bar->next[step & 1], (unsigned)chunk);
+            __syncthreads();
+            const int t0 = s_t;
+            __syncthreads();
+            if (t0 >= ntiles) break;
+            batch_tiles<P, NPT, SHIFT, FORCH>(cases, tiles, t0, min(t0 + chunk, ntiles), par0 ^ (step & 1), raw, cur);
+        }
+        if (step + 1 < nsteps || extra > 0)
+            if (!grid_barrier(bar, step, extra, limit, &s_ok)) return;
     }
 }
 

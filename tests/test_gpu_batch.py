@@ -1,4 +1,5 @@
-"""Batched form: independent cases advanced by one launch per step.
+"""Batched form: independent cases advanced together, one launch per step
+(graph mode) or one persistent launch per 32 steps (persistent mode).
 
 Each case runs the same per-node code as a single simulation, so after the
 same number of steps a batched case must equal its stand-alone run bit for
@@ -128,3 +129,59 @@ def test_every_tiling_gives_the_same_bits(prec):
             assert np.array_equal(a, b), (prec, c)
         s.close()
     batch.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_persistent_mode_equals_graph_mode_bit_for_bit(prec):
+    """The persistent launch (grid barrier between steps, coherent L2 loads)
+    runs the same per-node code: after 77 steps (two 32-step graphs and a
+    13-step launch) every case equals the graph-mode batch bit for bit, and
+    switching modes mid-run changes nothing either."""
+    from paper_2110_05943_gb300 import clb
+    spec, params, phis = _cases(prec)
+    bcs = [clb.clb_bc_cavity(1.0, 0.0) for _ in params]
+    ref = clb.Batch(params, phis, bcs)
+    per = clb.Batch(params, phis, bcs)
+    mix = clb.Batch(params, phis, bcs)
+    per.set_mode(clb.CLB_BATCH_PERSISTENT)
+    ref.step(77)
+    per.step(77)
+    mix.step(33)
+    mix.set_mode(clb.CLB_BATCH_PERSISTENT)
+    mix.step(44)
+    for c in range(len(params)):
+        want = ref.macros(c)
+        for other in (per, mix):
+            for a, b in zip(other.macros(c), want):
+                assert np.array_equal(a, b), (prec, c)
+    assert per.time == 77 and mix.time == 77
+    for b in (ref, per, mix):
+        b.close()
+
+
+def test_persistent_barrier_wait_expires_and_reports_timeout():
+    """Failure detection of the persistent mode: a step whose grid barrier
+    waits for one block more than the launch has (a flag nothing sets)
+    gives up after ~1 ms of SM clock, every block returns, and the call
+    reports CLB_ERR_TIMEOUT.  The context and the batch stay usable: the
+    state was not advanced, and stepping on gives the same bits as a batch
+    that never ran the test."""
+    from paper_2110_05943_gb300 import clb
+    spec, params, phis = _cases(2)
+    bcs = [clb.clb_bc_cavity(1.0, 0.0) for _ in params]
+    a = clb.Batch(params, phis, bcs)
+    ref = clb.Batch(params, phis, bcs)
+    a.set_mode(clb.CLB_BATCH_PERSISTENT)
+    a.step(40)
+    ref.step(40)
+    assert a.barrier_selftest(2_000_000) == clb.CLB_ERR_TIMEOUT
+    assert a.time == 40
+    a.sync()                                  # the flag was reported once and cleared
+    a.step(24)
+    ref.step(24)
+    for c in range(len(params)):
+        for x, y in zip(a.macros(c), ref.macros(c)):
+            assert np.array_equal(x, y), c
+    assert a.barrier_selftest(0) == clb.CLB_ERR_ARG          # bound outside 1 .. 4e9
+    a.close()
+    ref.close()
