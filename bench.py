@@ -19,10 +19,18 @@ clb_nusselt, wall-clock.  `--impl reference` times the FP64 CPU oracle on
 the host cores on a bounded sample of the same workload.
 
 Secondary objects on the same line: `forms` (FP16-storage forms at 8192^2),
-`batch` (512 seeded cavities in one launch per step), `cpu_baseline`,
-`steady_state` (time to steady state of each form on the Table 1 case) and
-`warm_start` (FP64 march from rest vs from the learned warm start on held-out
-cavities).  `--no-forms/--no-batch/--no-cpu/--no-steady/--no-warm` skip them.
+`accuracy` (FP16 forms against the FP64 path on the 8192^2 sigma 0.8 cavity
+at a fixed step count), `batch` (512 seeded cavities, graph and persistent
+launch modes), `mrt_cost` (the porous shift matrices against the unit-shift
+MRT limit, Table 2's comparison), `cavity64` (the 64^2 Table 1 cavity to
+steady state), `cpu_baseline` (all host cores and one), `steady_state` (time
+to steady state of each form on the Table 1 case), `warm_start` (FP64 march
+from rest vs from the learned warm start) and `surrogate_training`; the last
+key, `summary`, repeats their headline figures compactly.
+`--no-forms/--no-accuracy/--no-batch/--no-cpu/--no-steady/--no-warm/--no-mrt`
+skip them; `--validate-batch` adds the per-case Nusselt number of a
+stratified 64-case sample of the batch at steady state, FP16N against FP64.
+`--gpus N` without a launcher starts N local ranks itself (torchrun).
 """
 from __future__ import annotations
 
@@ -53,15 +61,17 @@ WORKLOAD = ("{n}x{n} porous cavity, seeded GRF porosity 0.3+0.6*Phi(g) (l=32, se
 # Algorithmic bytes per coupled cell update of the FP64 form: 14 distribution
 # values read and 14 written (8 B each) plus the porosity (8 B).
 BYTES_PER_CCU_F64 = 28 * 8 + 8
-# FP64 floating-point operations per coupled cell update executed by
-# k_step_f64<shift, forchheimer> (dadd + dmul + 2 dfma per launch / nodes,
-# ncu instruction counters; profiles/k_step_f64_cavity2048.md), and the FP64
-# pipe instructions (dadd + dmul + dfma) per node.
-FP64_FLOP_PER_CCU = 289.5
-FP64_INST_PER_CCU = 200.4
-# DRAM bytes per launch of k_step_f64 at 4096^2: 246.7 B/node measured by ncu
-# on the 2048^2 case (same kernel), scaled by the node count.
-DRAM_BYTES_PER_CCU_MEASURED = 246.7
+# FP64 floating-point operations per coupled cell update executed by the FP64
+# step kernel (dadd + dmul + 2 dfma per launch / nodes, ncu instruction
+# counters of the current kernel), and its FP64 pipe instructions (dadd +
+# dmul + dfma) per node.
+FP64_FLOP_PER_CCU = 261.5
+FP64_INST_PER_CCU = 179.4
+# DRAM bytes (read + write) per node of one launch of the current FP64 step
+# kernel, ncu on the 2048^2 case of the same workload, scaled by the node
+# count (traffic grows with the nodes): 14 + 14 values and the 64-byte
+# per-node constant table.
+DRAM_BYTES_PER_CCU_MEASURED = 280.4
 SMS, DFMA_PER_CLK_PER_SM = 152, 2   # GB300 FP64 pipe: 2 DFMA/clk/SM (1.25 TFLOP/s at 2.07 GHz)
 
 
@@ -147,14 +157,15 @@ def _porosity():
     return porosity_field(NX, NY, seed=PHI_SEED, ell=PHI_ELL)
 
 
-def cpu_oracle_rate(phi, budget_s: float = 12.0, side: int = 512):
+def cpu_oracle_rate(phi, budget_s: float = 12.0, side: int = 512, nthreads=None):
     """FP64 oracle on the SW corner block (side x side) of the workload, with
-    the full cavity's lattice parameters (L = n - 1); MLUPS on all host cores."""
+    the full cavity's lattice parameters (L = n - 1); MLUPS on all host cores
+    (nthreads None) or on the given number of threads."""
     side = min(side, NX)
     import oracle
     sub = phi[:side, :side].copy()
     p = oracle.Problem(nx=side, ny=side, L=float(NY - 1), **CASE)
-    o = oracle.Oracle(p, phi=sub)
+    o = oracle.Oracle(p, phi=sub, nthreads=nthreads)
     t0 = time.perf_counter()
     o.step(2)
     dt = max(time.perf_counter() - t0, 1e-6) / 2
@@ -246,12 +257,13 @@ FORMS = {  # storage form -> (precision code, algorithmic bytes per coupled cell
     "f16n": (2, 28 * 2 + 2 * 8 + 4),   # 14 FP16 deviations read+written, 8 B record read+written, FP32 1/phi
     "f16s": (1, 28 * 2 + 4),           # 14 FP16 deviations read+written, FP32 phi
 }
-# DRAM bytes (read + write) per node of one k_step2 launch, ncu on the 4096^2
-# case (profiles/k_step2_*_cavity4096.md); traffic grows with the node count.
-FORMS_DRAM_PER_NODE = {"f16n": 73.8, "f16s": 57.9}
-# DRAM bytes (read + write) of one k_step_batch launch on the 512-case workload
-# (45.0 M nodes, 8 x 16 blocks): 80.7 B/node, ncu (profiles/k_step_batch_cases512.md).
-BATCH_DRAM_PER_LAUNCH = 3.631e9
+# DRAM bytes (read + write) per node of one launch of the current FP16 step
+# kernels, ncu on the 4096^2 case of the same workload; traffic grows with
+# the node count.  None: not captured for the kernel as it stands.
+FORMS_DRAM_PER_NODE = {"f16n": None, "f16s": None}
+# DRAM bytes (read + write) per node of one launch of the current batch
+# kernel on the 512-case workload (ncu); None: not captured for this kernel.
+BATCH_DRAM_PER_NODE = None
 
 
 def reduced_precision_forms(clb, torch, args, hbm_peak, src):
@@ -281,61 +293,71 @@ def reduced_precision_forms(clb, torch, args, hbm_peak, src):
                      "dtype": "f32 arithmetic, f16 storage",
                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s",
                                   "frac": gbs / hbm_peak, "bytes_per_ccu": bpn,
-                                  "traffic": FORMS_DRAM_PER_NODE[name] * n * n,
+                                  "traffic": (FORMS_DRAM_PER_NODE[name] * n * n if FORMS_DRAM_PER_NODE[name] else None),
                                   "traffic_source": "ncu dram bytes per node at 4096^2 x nodes per launch",
                                   "kernel": f"k_step2<StoreH16{'N' if name == 'f16n' else ''}>",
                                   "peak_source": f"{src} hbm_gbs"}}
     return out
 
 
+def _batch_make(clb, torch, sel, prec):
+    stream = torch.cuda.current_stream()
+    params = [clb.clb_params_default(nx=c.nx, ny=c.ny, Ra=c.Ra, Da=c.Da, Pr=c.Pr, sigma=c.sigma, precision=prec)
+              for c in sel]
+    return clb.Batch(params, [c.phi for c in sel], [clb.clb_bc_cavity(1.0, 0.0) for _ in sel],
+                     stream=stream.cuda_stream)
+
+
+def _t_diff(c):
+    """Thermal diffusion time max(nx, ny)^2 / alpha of a batch case (alpha =
+    nu / Pr, nu from Eq. 46 with L = ny - 1): the time scale to steady state."""
+    nu = 0.1 * (c.ny - 1) * math.sqrt(c.Pr / (3.0 * c.Ra))
+    return max(c.nx, c.ny) ** 2 / (nu / c.Pr)
+
+
 def batched_form(clb, torch, args, hbm_peak, src):
     """512 seeded cavities of uneven size (sides log-uniform in [64, 1024],
     aspect 1-4; log10 Ra in [3, 6], log10 Da in [-4, -1], eps in [0.4, 0.9],
-    sigma in [0.5, 2], Pr 0.71) advanced by one FP16N launch per step with
-    the tiling chosen by clb_batch_tune; aggregate MLUPS over the timed
-    steps.  Accuracy: the 8 cases with the shortest diffusion time, as a
-    batch in FP64 and in FP16N, converged (criteria below); relative
+    sigma in [0.5, 2], Pr 0.71), FP16N, with the tiling chosen by
+    clb_batch_tune; aggregate MLUPS over the timed steps in both launch
+    modes (one launch per step replayed from graphs; one persistent launch
+    per 32 steps).  Accuracy: the 8 cases with the shortest diffusion time,
+    as a batch in FP64 and in FP16N, converged (criteria below); relative
     difference of the hot-wall Nusselt number per case."""
     from paper_2110_05943_gb300.inputs import batch_cases
     cases = batch_cases(512, seed=7)
     stream = torch.cuda.current_stream()
-
-    def make(sel, prec):
-        params = [clb.clb_params_default(nx=c.nx, ny=c.ny, Ra=c.Ra, Da=c.Da, Pr=c.Pr, sigma=c.sigma, precision=prec)
-                  for c in sel]
-        return clb.Batch(params, [c.phi for c in sel], [clb.clb_bc_cavity(1.0, 0.0) for _ in sel],
-                         stream=stream.cuda_stream)
-
-    b = make(cases, 2)
+    b = _batch_make(clb, torch, cases, 2)
     choice = b.tune(steps=3)
-    b.step(args.warmup)
-    torch.cuda.synchronize()
     steps = max(args.steps, 64)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    b.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
+    rates = {}
+    for mode, name in ((clb.CLB_BATCH_GRAPH, "graph"), (clb.CLB_BATCH_PERSISTENT, "persistent")):
+        b.set_mode(mode)
+        b.step(max(args.warmup, 32))
+        b.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        b.sync()
+        rates[name] = b.nodes * steps / (e0.elapsed_time(e1) / 1e3) / 1e6
     nodes = b.nodes
     nu = b.nusselt(0)
     b.close()
+    best = max(rates, key=rates.get)
     bpn = FORMS["f16n"][1]
-    gbs = bpn * nodes * steps / t / 1e9
+    gbs = bpn * rates[best] * 1e6 / 1e9
 
     # validation subset: the 8 cases with the shortest thermal diffusion time
-    # max(nx, ny)^2 / alpha (alpha = nu / Pr, nu from Eq. 46 with L = ny - 1)
-    def t_diff(c):
-        nu = 0.1 * (c.ny - 1) * math.sqrt(c.Pr / (3.0 * c.Ra))
-        return max(c.nx, c.ny) ** 2 / (nu / c.Pr)
-    quick = sorted(range(len(cases)), key=lambda i: t_diff(cases[i]))[:8]
+    quick = sorted(range(len(cases)), key=lambda i: _t_diff(cases[i]))[:8]
     sel = [cases[i] for i in quick]
     # FP64: to |dNu| <= 1e-6 Nu per 4000 steps.  FP16N: its time to steady by
     # the metric's |dNu| <= 1e-4 Nu per 1000 steps (its stochastic rounding
     # leaves Nu fluctuations of ~1e-5, so a tighter rule never fires), then
-    # on to the FP64 run's step count plus 40,000 and the mean Nu over the
+    # on to the FP64 run's step count plus 20,000 and the mean Nu over the
     # last 20,000 steps; errors are taken between those converged values.
-    v = make(sel, 0)
+    v = _batch_make(clb, torch, sel, 0)
     prev = v.nusselt(0)
     t0 = time.perf_counter()
     while v.time < 240_000:
@@ -346,7 +368,7 @@ def batched_form(clb, torch, args, hbm_peak, src):
         prev = nu64
     steps64, sec64 = v.time, time.perf_counter() - t0
     v.close()
-    v = make(sel, 2)
+    v = _batch_make(clb, torch, sel, 2)
     prev = v.nusselt(0)
     t0 = time.perf_counter()
     while v.time < 240_000:
@@ -365,12 +387,14 @@ def batched_form(clb, torch, args, hbm_peak, src):
     v.close()
     err = np.abs(nu16 / nu64 - 1)
     return {"workload": "512 seeded porous cavities (batch_cases seed 7), uneven grids, FP16N",
-            "value": nodes * steps / t / 1e6, "unit": UNIT, "steps": steps, "nodes_per_step": nodes,
-            "ms_per_step": t / steps * 1e3, "tile_choice": choice, "finite_cases": int(np.isfinite(nu).sum()),
+            "value": rates[best], "unit": UNIT, "mode": best, "mlups_by_mode": rates, "steps": steps,
+            "nodes_per_step": nodes, "ms_per_step": nodes / (rates[best] * 1e6) * 1e3, "tile_choice": choice,
+            "finite_cases": int(np.isfinite(nu).sum()),
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                         "bytes_per_ccu": bpn, "traffic": BATCH_DRAM_PER_LAUNCH,
-                         "traffic_source": "ncu dram bytes of one launch of this workload (tiling 9)",
-                         "kernel": "k_step_batch<StoreH16N>", "peak_source": f"{src} hbm_gbs"},
+                         "bytes_per_ccu": bpn,
+                         "traffic": BATCH_DRAM_PER_NODE * nodes if BATCH_DRAM_PER_NODE else None,
+                         "kernel": "k_step_batch / k_step_batch_persist <StoreH16N>",
+                         "peak_source": f"{src} hbm_gbs"},
             "validation": {"cases": [f"{c.nx}x{c.ny} Ra {c.Ra:.3g} Da {c.Da:.3g} eps {c.phi:.2f} sigma {c.sigma:.2f}"
                                      for c in sel],
                            "criterion": "FP64 |dNu| <= 1e-6 Nu / 4000 steps; FP16N time to |dNu| <= 1e-4 Nu / "
@@ -378,6 +402,176 @@ def batched_form(clb, torch, args, hbm_peak, src):
                            "nu_f64": [float(x) for x in nu64], "nu_f16n": [float(x) for x in nu16],
                            "max_rel_nu_error": float(np.nanmax(err)), "steps_f64": steps64,
                            "steps_f16n": steps16, "seconds_f64": sec64, "seconds_f16n": sec16}}
+
+
+def _batch_window_means(clb, torch, sel, prec, start, window=20, every=1000):
+    """Mean hot-wall Nu of each case over `window` samples `every` steps
+    apart, taken after step start[k] (cases with start None are retired);
+    the batch retires each case once its window is complete."""
+    n = len(sel)
+    b = _batch_make(clb, torch, sel, prec)
+    active = np.array([s is not None for s in start])
+    b.set_active(active.astype(np.int32))
+    sums, cnt = np.zeros(n), np.zeros(n, dtype=int)
+    while active.any():
+        b.step(every)
+        cur = b.nusselt(0)
+        for k in np.nonzero(active)[0]:
+            if b.time > start[k]:
+                sums[k] += cur[k]
+                cnt[k] += 1
+        done = active & (cnt >= window)
+        if done.any():
+            active &= ~done
+            b.set_active(active.astype(np.int32))
+    b.close()
+    return np.where(cnt > 0, sums / np.maximum(cnt, 1), np.nan)
+
+
+def batch_validation(clb, torch, n=64, cap=200_000):
+    """Per-case hot-wall Nusselt number of a stratified sample of the
+    512-case batch at steady state, FP16N against FP64: the cases sorted by
+    thermal diffusion time, split into n strata of 512 / n, the fastest of
+    each taken.  A case is steady at the first multiple of 2000 steps at
+    which its FP64 Nu changed by at most 1e-6 Nu over the last 2000 steps
+    (cap `cap` steps).  Each form's Nu is then the mean of 20 samples over
+    the same 20,000 steps after that point (the stochastic rounding of the
+    FP16 form leaves Nu fluctuations of ~1e-5, and a flow that still
+    oscillates slowly is compared over the same window)."""
+    from paper_2110_05943_gb300.inputs import batch_cases
+    cases = batch_cases(512, seed=7)
+    order = sorted(range(len(cases)), key=lambda i: _t_diff(cases[i]))
+    per = len(cases) // n
+    idx = [order[k * per] for k in range(n)]
+    sel = [cases[i] for i in idx]
+    t0 = time.perf_counter()
+    b = _batch_make(clb, torch, sel, 0)
+    active = np.ones(n, dtype=bool)
+    at = [None] * n
+    prev = b.nusselt(0)
+    while active.any() and b.time < cap:
+        b.step(2000)
+        cur = b.nusselt(0)
+        hit = active & (np.abs(cur - prev) <= 1e-6 * np.abs(cur))
+        for k in np.nonzero(hit)[0]:
+            at[k] = b.time
+        if hit.any():
+            active &= ~hit
+            b.set_active(active.astype(np.int32))
+        prev = cur
+    b.close()
+    nu64 = _batch_window_means(clb, torch, sel, 0, at)
+    s64 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    nu16 = _batch_window_means(clb, torch, sel, 2, at)
+    s16 = time.perf_counter() - t0
+    ok = [k for k in range(n) if at[k] is not None]
+    err = {k: abs(nu16[k] / nu64[k] - 1) for k in ok}
+    return {"workload": f"{n} of the 512 batch cavities, stratified by thermal diffusion time "
+                        f"(fastest of each stratum of {per})",
+            "criterion": f"steady: FP64 |dNu| <= 1e-6 Nu over 2000 steps (cap {cap} steps); each form's Nu = "
+                         "mean of 20 samples over the next 20,000 steps",
+            "cases": [{"case": int(i), "grid": f"{cases[i].nx}x{cases[i].ny}", "Ra": round(cases[i].Ra, 1),
+                       "Da": float(f"{cases[i].Da:.3g}"), "steady_at": at[k],
+                       "nu_f64": None if at[k] is None else float(nu64[k]),
+                       "nu_f16n": None if at[k] is None else float(nu16[k]), "rel_err": err.get(k)}
+                      for k, i in enumerate(idx)],
+            "converged": len(ok), "max_rel_nu_error": max(err.values()) if err else None,
+            "median_rel_nu_error": float(np.median(list(err.values()))) if err else None,
+            "within_1e-4": int(sum(e <= 1e-4 for e in err.values())), "seconds_f64": s64, "seconds_f16n": s16}
+
+
+def accuracy_forms(clb, torch, n=8192, steps=1000):
+    """The FP16-storage forms against the FP64 path (parity-tested against
+    the oracle) on the n^2 seeded cavity with sigma 0.8 (Da 1e-3, Ra 1e6,
+    Pr 0.71) after the same number of steps: max |a - b| of u_x, u_y over
+    the grid, relative to max |u| of the FP64 field and to the velocity
+    scale u_c = Ma c_s of Eq. 46; max |T_a - T_b| (the walls differ by dT =
+    1); the relative difference of the hot-wall Nusselt number; and each
+    form's time per step."""
+    from paper_2110_05943_gb300.inputs import porosity_field
+    phi = porosity_field(n, n, seed=PHI_SEED, ell=PHI_ELL)
+    stream = torch.cuda.current_stream()
+    uc = 0.1 / math.sqrt(3.0)
+    ref = None
+    out = {"workload": f"{n}x{n} porous cavity, seeded GRF porosity, Da 1e-3, Ra 1e6, Pr 0.71, sigma 0.8",
+           "steps": steps, "u_c": uc}
+    for name, prec in (("f64", 0), ("f16n", 2), ("f16s", 1)):
+        p = clb.clb_params_default(nx=n, ny=n, Ra=1e6, Da=1e-3, Pr=0.71, sigma=0.8, precision=prec)
+        sim = clb.Simulation.create(p, phi, clb.clb_bc_cavity(1.0, 0.0), stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        f = torch.empty((3, n, n), dtype=torch.float64, device="cuda")
+        clb.clb_macros_device(sim.handle, None, f[0].data_ptr(), f[1].data_ptr(), f[2].data_ptr())
+        nu = sim.nusselt(clb.W)
+        sim.close()
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = (f, nu, float(f[:2].abs().max()))
+            out[name] = {"ms_per_step": ms, "nu": nu, "max_abs_u": ref[2]}
+            continue
+        du = [float((f[k] - ref[0][k]).abs().max()) for k in range(2)]
+        out[name] = {"ms_per_step": ms, "nu": nu, "max_abs_err_ux": du[0], "max_abs_err_uy": du[1],
+                     "rel_err_u": max(du) / ref[2], "err_u_over_uc": max(du) / uc,
+                     "max_abs_err_T": float((f[2] - ref[0][2]).abs().max()), "rel_err_nu": abs(nu / ref[1] - 1),
+                     "speedup_vs_f64": out["f64"]["ms_per_step"] / ms}
+        del f
+    del ref
+    torch.cuda.empty_cache()
+    return out
+
+
+def mrt_cost(clb, torch, steps=32):
+    """Cost of the porous shift matrices: the FP64 step on the bench workload
+    with the shift (N, N_T of Eqs. 14, 31) and in the unit-shift limit (N =
+    N_T = I, the MRT scheme named at the end of Sec. 2), CUDA-event time per
+    step; Table 2 of the paper reports the ratio on a CPU."""
+    phi = _porosity()
+    stream = torch.cuda.current_stream()
+    ms = {}
+    for name, shift in (("clb", 1), ("mrt", 0)):
+        p = clb.clb_params_default(nx=NX, ny=NY, shift=shift, **CASE)
+        sim = clb.Simulation.create(p, phi, clb.clb_bc_cavity(1.0, 0.0), stream=stream.cuda_stream)
+        sim.step(4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[name] = e0.elapsed_time(e1) / steps
+        sim.close()
+    return {"workload": WORKLOAD.format(n=NX), "ms_per_step_clb": ms["clb"], "ms_per_step_mrt": ms["mrt"],
+            "ratio_clb_over_mrt": ms["clb"] / ms["mrt"],
+            "paper_cpu_ratio": "2099.33 s / 1812.31 s = 1.158 (Table 2, i5-8400)"}
+
+
+def cavity64(clb, torch, cap=20_000, every=100):
+    """The 64^2 porous cavity (phi 0.6, Da 1e-2, Ra 1e4, Pr 1, sigma 1):
+    20,000 steps or until max(r_u, r_T) over `every` steps drops below 1e-8;
+    mean Nusselt number of both isothermal walls (Table 1 "Present" at 128^2:
+    1.4873)."""
+    p = clb.clb_params_default(nx=64, ny=64, Ra=1e4, Da=1e-2, Pr=1.0, sigma=1.0)
+    sim = clb.Simulation.create(p, 0.6, clb.clb_bc_cavity(1.0, 0.0),
+                                stream=torch.cuda.current_stream().cuda_stream)
+    t0 = time.perf_counter()
+    r = (1.0, 1.0)
+    while sim.time < cap:
+        sim.step(every)
+        r = sim.residual()
+        if max(r) < 1e-8:
+            break
+    sec = time.perf_counter() - t0
+    out = {"workload": "64x64 cavity, phi 0.6, Da 1e-2, Ra 1e4, Pr 1, sigma 1, FP64",
+           "criterion": "20,000 steps or max(r_u, r_T) < 1e-8 over 100 steps", "steps": sim.time,
+           "residual": max(r), "seconds": sec, "nu_hot": sim.nusselt(clb.W), "nu_cold": sim.nusselt(clb.E)}
+    sim.close()
+    return out
 
 
 def warm_start_form(clb, torch, ncase=4):
@@ -458,8 +652,55 @@ def surrogate_training(torch, bf16_peak, src, batch=16, steps=20):
                          "peak_source": f"{src} bf16_tflops"}}
 
 
+def _summary(line):
+    """Headline figures of every section, compact (the last key of the line)."""
+    r3 = lambda v: None if v is None else float(f"{v:.4g}")
+    s = {"f64_4096": {"mlups": r3(line["value"]), "frac": r3(line["roofline"]["frac"]),
+                      "bound": line["roofline"]["bound"],
+                      "fp64_pipe_frac": r3(line["roofline"].get("fp64_pipe_frac")),
+                      "e2e_mlups": r3((line.get("e2e") or {}).get("value"))}}
+    for name, f in (line.get("forms") or {}).items():
+        s[f"{name}_8192"] = {"mlups": r3(f["value"]), "hbm_frac": r3(f["roofline"]["frac"])}
+    for key, tag in (("accuracy", "acc_8192"), ("accuracy_2048", "acc_2048")):
+        a = line.get(key)
+        if a:
+            s[tag] = {k: {"u_rel": r3(a[k]["rel_err_u"]), "u_uc": r3(a[k]["err_u_over_uc"]),
+                          "T": r3(a[k]["max_abs_err_T"]), "nu": r3(a[k]["rel_err_nu"])} for k in ("f16n", "f16s")}
+            s[tag]["steps"] = a["steps"]
+    b = line.get("batch")
+    if b:
+        s["batch_512"] = {"mlups": r3(b["value"]), "mode": b["mode"], "hbm_frac": r3(b["roofline"]["frac"]),
+                          "by_mode": {k: r3(v) for k, v in b["mlups_by_mode"].items()},
+                          "max_rel_nu_err_8": r3(b["validation"]["max_rel_nu_error"])}
+    v = line.get("batch_validation")
+    if v:
+        s["batch_validation"] = {"converged": v["converged"], "of": len(v["cases"]),
+                                 "max_rel_nu_err": r3(v["max_rel_nu_error"]), "within_1e-4": v["within_1e-4"]}
+    m = line.get("mrt_cost")
+    if m:
+        s["clb_over_mrt"] = r3(m["ratio_clb_over_mrt"])
+    c = line.get("cavity64")
+    if c:
+        s["cavity64_nu"] = r3(c["nu_hot"])
+    st = line.get("steady_state")
+    if st:
+        s["steady_128"] = {k: {"rel_nu": r3(f.get("rel_nu_converged_vs_f64")), "speedup": r3(f.get("speedup_vs_f64"))}
+                           for k, f in st["forms"].items() if k != "f64"}
+    cb = line.get("cpu_baseline")
+    if cb:
+        s["oracle_mlups"] = {"cores": cb["cores"], "all": r3(cb["value"]),
+                             "one": r3((line.get("cpu_baseline_1core") or {}).get("value"))}
+    w = line.get("warm_start")
+    if w:
+        s["warm_start"] = {"steps_ratio": r3(w["steps_ratio_total"]), "wall_speedup": r3(w["wall_speedup_total"]),
+                           "max_rel_nu": r3(w["max_rel_nu"])}
+    t = line.get("surrogate_training")
+    if t:
+        s["surrogate_tflops"] = r3(t["roofline"]["achieved"])
+    return s
+
+
 def run_ours(args):
-    import numpy as np
     import torch
 
     ws, rank, local = _dist()
@@ -543,47 +784,75 @@ def run_ours(args):
     if args.precision != "f64":
         bpn = FORMS[args.precision][1]
         gb = bpn * cells / per_launch / 1e9
+        tr = FORMS_DRAM_PER_NODE[args.precision]
         roof = {"bound": "hbm", "achieved": gb, "peak": hbm_peak, "unit": "GB/s", "frac": gb / hbm_peak,
-                "traffic": FORMS_DRAM_PER_NODE[args.precision] * cells,
-                "kernel": f"k_step2<{args.precision}>", "bytes_per_ccu": bpn,
-                "peak_source": f"{src} hbm_gbs"}
-    elif FP64_FLOP_PER_CCU:
+                "traffic": tr * cells if tr else None, "kernel": f"k_step2<{args.precision}>",
+                "bytes_per_ccu": bpn, "peak_source": f"{src} hbm_gbs"}
+    else:
         ach = FP64_FLOP_PER_CCU * cells / per_launch / 1e12
         inst_rate = FP64_INST_PER_CCU * cells / per_launch
         inst_peak = SMS * DFMA_PER_CLK_PER_SM * sm_mhz * 1e6
         roof = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
-                "traffic": DRAM_BYTES_PER_CCU_MEASURED * cells if NX == 4096 else None,
-                "kernel": "k_step_f64<shift, forchheimer>", "flop_per_ccu": FP64_FLOP_PER_CCU,
+                "traffic": DRAM_BYTES_PER_CCU_MEASURED * cells,
+                "kernel": "k_step<StoreF64, shift, forchheimer>", "flop_per_ccu": FP64_FLOP_PER_CCU,
                 "peak_source": f"FP64 pipe: {SMS} SMs x {DFMA_PER_CLK_PER_SM} DFMA/clk x 2 flop x {sm_mhz:.0f} MHz "
-                               "(median SM clock in the timed region; FMA probe measured 1.253 TFLOP/s)",
+                               "(median SM clock, timed region)",
                 "fp64_pipe_frac": inst_rate / inst_peak,
                 "hbm": {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                         "bytes_per_ccu": BYTES_PER_CCU_F64, "peak_source": f"{src} hbm_gbs"}}
-    else:
-        roof = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
-                "traffic": None, "kernel": "k_step_f64<shift, forchheimer>", "bytes_per_ccu": BYTES_PER_CCU_F64,
-                "peak_source": f"{src} hbm_gbs"}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t / args.steps * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "f64" else "f32 arithmetic, f16 storage", "data": "synthetic",
-            "config": {"workload": WORKLOAD.format(n=NX).replace("FP64", args.precision.upper()), "nx": NX, "ny": NY, "cells": cells, "replicas": ws,
-                       "l2": f"state {NX * NY * 14 * 16 / 1e9:.2f} GB per replica (two buffers) vs 0.13 GB L2: no flush",
+            "config": {"workload": f"{NX}x{NY} porous cavity, seeded GRF porosity, Ra 1e6, Da 1e-3, Pr 0.71, "
+                                   f"sigma 1, {args.precision.upper()}",
+                       "porosity": "0.3+0.6*Phi(g), g Gaussian random field l=32, seed 20211012",
+                       "nx": NX, "ny": NY, "cells": cells, "replicas": ws,
+                       "l2": f"state {NX * NY * 14 * 16 / 1e9:.2f} GB per replica (two buffers) vs 0.13 GB L2: "
+                             "no flush",
                        "parallelism": f"replicas x{ws}", "nu_hot_wall_after": nu},
             "roofline": roof, "clocks": clocks, "gpu_launches": args.steps,
             "e2e": e2e}
-    if not args.no_forms:
-        line["forms"] = reduced_precision_forms(clb, torch, args, hbm_peak, src)
-    if not args.no_batch:
-        line["batch"] = batched_form(clb, torch, args, hbm_peak, src)
     if ws == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_oracle_rate(phi)
+        line["cpu_baseline_1core"] = cpu_oracle_rate(phi, budget_s=8.0, side=256, nthreads=1)
+    if not args.no_forms:
+        line["forms"] = reduced_precision_forms(clb, torch, args, hbm_peak, src)
+    if not args.no_accuracy:
+        # the literal precision workload (at 1000 steps its flow has barely
+        # started: max |u| ~ 1e-4), and a 2048^2 one run until the flow is
+        # developed
+        line["accuracy"] = accuracy_forms(clb, torch, n=8192, steps=1000)
+        line["accuracy_2048"] = accuracy_forms(clb, torch, n=2048, steps=30_000)
+    if not args.no_batch:
+        line["batch"] = batched_form(clb, torch, args, hbm_peak, src)
+    if args.validate_batch:
+        line["batch_validation"] = batch_validation(clb, torch)
+    if not args.no_mrt:
+        line["mrt_cost"] = mrt_cost(clb, torch)
+        line["cavity64"] = cavity64(clb, torch)
     if not args.no_steady:
         line["steady_state"] = steady_state_forms(clb, torch)
     if not args.no_warm and ws == 1:
         line["warm_start"] = warm_start_form(clb, torch)
         line["surrogate_training"] = surrogate_training(torch, float(peaks.get("bf16_tflops", 1900.0)), src)
+    line["summary"] = _summary(line)
     print(json.dumps(line), flush=True)
+
+
+def _free_port() -> int:
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def launch_ranks(gpus: int, argv) -> int:
+    """Run this script on `gpus` local ranks under torch.distributed.run
+    (one process per GPU, rendezvous on 127.0.0.1); returns its exit code."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+           "--master-addr=127.0.0.1", f"--master-port={_free_port()}", os.path.abspath(__file__)] + list(argv)
+    return subprocess.call(cmd)
 
 
 def main():
@@ -596,8 +865,12 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-steady", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the FP16-storage forms at 8192^2")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the FP16-vs-FP64 accuracy run at 8192^2")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-case batch")
+    ap.add_argument("--no-mrt", action="store_true", help="skip the MRT cost ratio and the 64^2 cavity")
     ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--validate-batch", action="store_true",
+                    help="add the stratified 64-case steady-state Nusselt validation of the batch (minutes)")
     ap.add_argument("--size", type=int, default=4096, help="grid side (default 4096; smaller for profiling)")
     ap.add_argument("--precision", choices=("f64", "f16s", "f16n"), default="f64",
                     help="storage form of the main measurement (default f64, the reported workload)")
@@ -606,6 +879,14 @@ def main():
     NX = NY = args.size
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.gpus < 1:
+        ap.error("--gpus must be >= 1")
+    ws = os.environ.get("WORLD_SIZE")
+    if ws is None:
+        if args.gpus > 1:
+            raise SystemExit(launch_ranks(args.gpus, sys.argv[1:]))
+    elif int(ws) != args.gpus:
+        raise SystemExit(f"bench.py: --gpus {args.gpus} but the launcher started WORLD_SIZE={ws} ranks")
     if args.impl == "reference":
         run_reference(args)
     else:

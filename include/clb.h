@@ -217,10 +217,13 @@ void clb_destroy(clb_handle* h);
 typedef struct clb_batch clb_batch;
 /* Launch modes of a batch (clb_batch_set_mode):
  *   CLB_BATCH_GRAPH      : one launch per step, replayed from CUDA graphs
- *                          of 32 steps (the default);
- *   CLB_BATCH_PERSISTENT : one cooperative launch (all blocks resident)
- *                          per 32 steps, itself captured in a CUDA graph,
- *                          whose steps are separated by a grid barrier.  A
+ *                          of 32 steps;
+ *   CLB_BATCH_PERSISTENT : (the default) one cooperative launch (all
+ *                          blocks resident) per 32 steps, itself captured
+ *                          in a CUDA graph, whose steps are separated by a
+ *                          grid barrier; the blocks claim tiles from a
+ *                          counter.  If the device cannot co-schedule the
+ *                          grid, the batch falls back to CLB_BATCH_GRAPH.  A
  *                          barrier wait is bounded (about 2 s); if it
  *                          expires the launch stops, and the next call that
  *                          waits for the batch (clb_batch_sync,

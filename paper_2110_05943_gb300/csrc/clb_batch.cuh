@@ -30,7 +30,7 @@ struct clb_batch {
     int per_cta = 8;                // tiles per CTA
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
-    int mode = CLB_BATCH_GRAPH;
+    int mode = CLB_BATCH_PERSISTENT;   // measured faster on the 512-case workload (30.4 vs 30.0 GLUPS, FP16N)
     GridBarrier* bar = nullptr;     // persistent mode: grid barrier state (device)
     int pgrid = 0;                  // persistent mode: resident blocks of the launch
     long long wait_limit = 4000000000LL;   // barrier wait bound, SM cycles (~2 s)
@@ -315,7 +315,15 @@ extern "C" int clb_batch_step(clb_batch* b, int64_t n) {
             left -= kGraphSteps;
         } else if (b->mode == CLB_BATCH_PERSISTENT) {
             const int k = (int)std::min<int64_t>(left, kGraphSteps);
-            CKB(b, batch_persist(b, b->stream, b->par, k, 0, b->wait_limit));
+            const cudaError_t e = batch_persist(b, b->stream, b->par, k, 0, b->wait_limit);
+            if (e == cudaErrorCooperativeLaunchTooLarge || e == cudaErrorNotSupported) {
+                // the device cannot hold the whole grid at once: step by launches instead
+                cudaGetLastError();
+                b->mode = CLB_BATCH_GRAPH;
+                batch_drop_graphs(b);
+                continue;
+            }
+            CKB(b, e);
             b->par ^= k & 1;
             left -= k;
         } else {

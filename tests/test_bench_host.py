@@ -75,3 +75,53 @@ def test_reference_arm_rank_zero_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_gpus_flag_without_launcher_starts_that_many_ranks():
+    """`bench.py --gpus 2` run directly starts two local ranks itself
+    (torch.distributed.run on 127.0.0.1); the reference arm's rank 0 prints
+    one line that reports both, the other rank prints nothing."""
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "LOCAL_RANK", "WORLD_SIZE", "MASTER_ADDR",
+                                                           "MASTER_PORT")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2",
+                        "--steps", "1", "--warmup", "3", "--size", "256"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout
+    assert json.loads(lines[0])["n_gpus"] == 2
+
+
+def test_gpus_flag_must_match_the_launcher():
+    r = _reference({"RANK": "0", "LOCAL_RANK": "0", "WORLD_SIZE": "1"}, "--gpus", "2", "--steps", "1",
+                   "--warmup", "3")
+    assert r.returncode != 0 and "WORLD_SIZE=1" in (r.stderr + r.stdout)
+
+
+def test_summary_is_compact_and_complete():
+    """The line's last key repeats every section's headline figure in a few
+    hundred bytes (the part of the line a log tail keeps)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    roof = {"frac": 0.7, "bound": "alu", "fp64_pipe_frac": 0.9}
+    line = {"value": 3000.0, "roofline": roof, "e2e": {"value": 2000.0},
+            "forms": {"f16n": {"value": 46000.0, "roofline": {"frac": 0.52}},
+                      "f16s": {"value": 77000.0, "roofline": {"frac": 0.68}}},
+            "accuracy": {"steps": 1000, **{k: {"rel_err_u": 1e-3, "err_u_over_uc": 2e-5, "max_abs_err_T": 1e-4,
+                                               "rel_err_nu": 1e-5} for k in ("f16n", "f16s")}},
+            "accuracy_2048": {"steps": 30000, **{k: {"rel_err_u": 1e-3, "err_u_over_uc": 2e-5,
+                                                     "max_abs_err_T": 1e-4, "rel_err_nu": 1e-5}
+                                                 for k in ("f16n", "f16s")}},
+            "batch": {"value": 30000.0, "mode": "persistent", "roofline": {"frac": 0.34},
+                      "mlups_by_mode": {"graph": 29000.0, "persistent": 30000.0},
+                      "validation": {"max_rel_nu_error": 1e-5}},
+            "mrt_cost": {"ratio_clb_over_mrt": 1.1}, "cavity64": {"nu_hot": 1.49},
+            "steady_state": {"forms": {"f64": {}, "f16n": {"rel_nu_converged_vs_f64": 1e-6, "speedup_vs_f64": 2.0}}},
+            "cpu_baseline": {"cores": 16, "value": 38.0}, "cpu_baseline_1core": {"value": 3.0},
+            "warm_start": {"steps_ratio_total": 0.8, "wall_speedup_total": 1.2, "max_rel_nu": 1e-5},
+            "surrogate_training": {"roofline": {"achieved": 34.0}}}
+    s = bench._summary(line)
+    for k in ("f64_4096", "f16n_8192", "f16s_8192", "acc_8192", "acc_2048", "batch_512", "clb_over_mrt",
+              "cavity64_nu", "steady_128", "oracle_mlups", "warm_start", "surrogate_tflops"):
+        assert k in s, k
+    assert len(json.dumps(s)) < 1400

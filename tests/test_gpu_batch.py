@@ -143,7 +143,9 @@ def test_persistent_mode_equals_graph_mode_bit_for_bit(prec):
     ref = clb.Batch(params, phis, bcs)
     per = clb.Batch(params, phis, bcs)
     mix = clb.Batch(params, phis, bcs)
+    ref.set_mode(clb.CLB_BATCH_GRAPH)
     per.set_mode(clb.CLB_BATCH_PERSISTENT)
+    mix.set_mode(clb.CLB_BATCH_GRAPH)
     ref.step(77)
     per.step(77)
     mix.step(33)
