@@ -293,6 +293,7 @@ template <typename R>
 CLB_HD R sqrt_guard() { return R(0); }
 template <>
 CLB_HD double sqrt_guard<double>() { return 1e-300; }
+
 __device__ __forceinline__ float recip(float x) { return __fdividef(1.0f, x); }
 __device__ __forceinline__ float sqroot(float x) {
     float r;
@@ -423,7 +424,8 @@ CLB_HD Incr9T<R> collide9_incr(const Mom9T<R>& k, R rho, R X, R Y, R hFx, R hFy,
         A = fma(R(4) * XY, k.k11, A);
         A = fma(-Y2p, k.k21, A);
         A = fma(-X2p, k.k12, A);
-        A = fma(-(ip * XY), w + Xjy, A);
+        const R ipXY = ip * XY;
+        A = fma(-ipXY, w + Xjy, A);
         const R c8 = fma(ip, A, k.k22);
         // increments of Eq. 11 (Lambda of Eq. 15, s_0 = s_1 = 1); the
         // (k20, k02) block relaxes towards rho / 3 each:
@@ -448,7 +450,7 @@ CLB_HD Incr9T<R> collide9_incr(const Mom9T<R>& k, R rho, R X, R Y, R hFx, R hFy,
         B = fma(R(4) * XY, D5, B);
         B = fma(Y2p, D6, B);
         B = fma(X2p, D7, B);
-        B = fma(ipX2 * Y, fma(Y, D1, XD2), B);
+        B = fma((ipXY + ipXY), fma(Y, D1, XD2), B);
         r.r8 = fma(ip, B, D8);
     } else {
         // unit shift: relax raw moments towards Eq. 19's m^eq with Eq. 19's S
@@ -482,7 +484,7 @@ CLB_HD void apply9(R (&f)[9], const Incr9T<R>& r) {
     const R pa = r.r3 - r.r8, qa = r.r1 - r.r7;
     const R pb = r.r4 - r.r8, qb = r.r2 - r.r6;
     const R u1 = r.r8 + r.r5, u2 = r.r8 - r.r5, v1 = r.r6 + r.r7, v2 = r.r6 - r.r7;
-    f[0] += (r.r8 - r.r3) - r.r4;
+    f[0] = (f[0] - pa) - r.r4;                  // f0 + r8 - r3 - r4
     f[1] = fma(R(0.5), pa + qa, f[1]);
     f[3] = fma(R(0.5), pa - qa, f[3]);
     f[2] = fma(R(0.5), pb + qb, f[2]);
@@ -510,15 +512,17 @@ CLB_HD void collide9(R (&f)[9], const Mom9T<R>& k, R rho, R X, R Y, R hFx, R hFy
 // of the pre-collision g are used.
 template <typename R, bool SHIFT>
 CLB_HD void collide5(R (&g)[5], R n0, R T, R X, R Y, const PhysT<R>& P) {
-    const R h1 = fma(P.hom, g[1] - g[3], P.hza * (X * T));
-    const R h2 = fma(P.hom, g[2] - g[4], P.hza * (Y * T));
+    const R hzT = P.hza * T;
+    const R h1 = fma(P.hom, g[1] - g[3], hzT * X);
+    const R h2 = fma(P.hom, g[2] - g[4], hzT * Y);
+    const R X2 = X * X, Y2 = Y * Y;
     R h3, h4;
     if (SHIFT) {
-        h3 = fma(X + X, h1, T * fma(R(-0.5) * X, X, P.hcT2));
-        h4 = fma(Y + Y, h2, T * fma(R(-0.5) * Y, Y, P.hcT2));
+        h3 = fma(X + X, h1, T * fma(R(-0.5), X2, P.hcT2));
+        h4 = fma(Y + Y, h2, T * fma(R(-0.5), Y2, P.hcT2));
     } else {
-        h3 = T * fma(R(0.5) * X, X, P.hcT2);
-        h4 = T * fma(R(0.5) * Y, Y, P.hcT2);
+        h3 = T * fma(R(0.5), X2, P.hcT2);
+        h4 = T * fma(R(0.5), Y2, P.hcT2);
     }
     g[0] = fma(R(-2), h3 + h4, n0);
     g[1] = h3 + h1;
