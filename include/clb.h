@@ -216,14 +216,14 @@ void clb_destroy(clb_handle* h);
  * data-parallel way to run parameter studies such as its Table 1. */
 typedef struct clb_batch clb_batch;
 /* Launch modes of a batch (clb_batch_set_mode):
- *   CLB_BATCH_GRAPH      : one launch per step, replayed from CUDA graphs
- *                          of 32 steps;
- *   CLB_BATCH_PERSISTENT : (the default) one cooperative launch (all
- *                          blocks resident) per 32 steps, itself captured
- *                          in a CUDA graph, whose steps are separated by a
- *                          grid barrier; the blocks claim tiles from a
- *                          counter.  If the device cannot co-schedule the
- *                          grid, the batch falls back to CLB_BATCH_GRAPH.  A
+ *   CLB_BATCH_GRAPH      : (the default) one launch per step, replayed
+ *                          from CUDA graphs of 32 steps;
+ *   CLB_BATCH_PERSISTENT : one cooperative launch (all blocks resident)
+ *                          per 32 steps, itself captured in a CUDA graph,
+ *                          whose steps are separated by a grid barrier; the
+ *                          blocks claim tiles from a counter.  If the
+ *                          device cannot co-schedule the grid, the batch
+ *                          falls back to CLB_BATCH_GRAPH.  A
  *                          barrier wait is bounded (about 2 s); if it
  *                          expires the launch stops, and the next call that
  *                          waits for the batch (clb_batch_sync,

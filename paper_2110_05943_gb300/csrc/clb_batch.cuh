@@ -30,7 +30,7 @@ struct clb_batch {
     int per_cta = 8;                // tiles per CTA
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
-    int mode = CLB_BATCH_PERSISTENT;   // measured faster on the 512-case workload (30.4 vs 30.0 GLUPS, FP16N)
+    int mode = CLB_BATCH_GRAPH;   // measured faster on the 512-case workload (FP16N 30.8 vs 30.1 GLUPS)
     GridBarrier* bar = nullptr;     // persistent mode: grid barrier state (device)
     int pgrid = 0;                  // persistent mode: resident blocks of the launch
     long long wait_limit = 4000000000LL;   // barrier wait bound, SM cycles (~2 s)

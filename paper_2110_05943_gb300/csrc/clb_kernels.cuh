@@ -631,7 +631,9 @@ __device__ __forceinline__ PhysT<f2> splat(const PhysT<float>& p) {
 __device__ __forceinline__ constexpr bool column_dir(int i) { return i == 0 || i == 2 || i == 4; }
 
 // ---------------------------------------------------------------- storage
-// Loads of the distribution buffers.  A kernel that only reads its input
+// Loads of the distribution buffers (stores use __stwb: explicitly global
+// even where the pointer comes from shared memory, as in the batch
+// kernels).  A kernel that only reads its input
 // buffer takes the read-only (non-coherent) cache path.  The persistent
 // batch kernel reads, in one step, what other blocks wrote in the step
 // before, which the read-only path does not allow; it uses ordinary
@@ -658,7 +660,7 @@ struct LdCG {
 
 struct LdCA {
     template <class T>
-    static __device__ __forceinline__ T ld(const T* p) { return *p; }
+    static __device__ __forceinline__ T ld(const T* p) { return __ldca(p); }
     static __device__ __forceinline__ double ld_again(const double* p) {
         double v;
         asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
@@ -708,9 +710,9 @@ struct StoreF64T {
                                                  const R (&f)[9], const R (&g)[5], R, R, R, R, R, uint32_t) {
         const long long o = (long long)y * K.g.px + x;
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * K.g.plane + o] = f[i];
+        for (int i = 0; i < 9; ++i) __stwb(B.f + i * K.g.plane + o, f[i]);
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * K.g.plane + o] = g[i];
+        for (int i = 0; i < 5; ++i) __stwb(B.g + i * K.g.plane + o, g[i]);
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
@@ -773,9 +775,9 @@ struct StoreH16T {
         const int o = y * K.g.px + x, Q = (int)K.g.plane;
         const Dither d = dither_for((uint32_t)o, seq);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - K.wf[i]) * kDevScale, dword(d, i));
+        for (int i = 0; i < 9; ++i) __stwb(B.f + i * Q + o, sr_half((f[i] - K.wf[i]) * kDevScale, dword(d, i)));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half(g[i] * kDevScale, dword(d, 9 + i));
+        for (int i = 0; i < 5; ++i) __stwb(B.g + i * Q + o, sr_half(g[i] * kDevScale, dword(d, 9 + i)));
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
@@ -814,12 +816,12 @@ struct StoreH16T {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const f2 d = fma(f[i], f2(kDevScale), f2(-K.wfs[i]));   // (f - w_i rho_0) 2^12
-            *reinterpret_cast<__half2*>(B.f + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, i));
+            __stwb(reinterpret_cast<__half2*>(B.f + i * Q + o), sr_half2(d.lo(), d.hi(), dword(rw, i)));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const f2 d = g[i] * f2(kDevScale);
-            *reinterpret_cast<__half2*>(B.g + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, 9 + i));
+            __stwb(reinterpret_cast<__half2*>(B.g + i * Q + o), sr_half2(d.lo(), d.hi(), dword(rw, 9 + i)));
         }
     }
 };
@@ -928,7 +930,7 @@ struct StoreH16NT {
         uint2 r;
         r.x = *reinterpret_cast<const unsigned int*>(&a);
         r.y = *reinterpret_cast<const unsigned int*>(&b);
-        B.rec[o] = r;
+        __stwb(B.rec + o, r);
         // same per-direction formulas, on the same rounded record, as pull_one
         const float2 fa = __half22float2(a), fb = __half22float2(b);
         const float br = 1.0f + fa.x, bX = fa.y, bY = fb.x, bT = fb.y;
@@ -942,9 +944,9 @@ struct StoreH16NT {
                              geqc_comp<4>(bT, bX, bY, s, c, t0)};
         const Dither d = dither_for((uint32_t)o, seq);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) B.f[i * Q + o] = sr_half((f[i] - fe[i]) * kDevScale, dword(d, i));
+        for (int i = 0; i < 9; ++i) __stwb(B.f + i * Q + o, sr_half((f[i] - fe[i]) * kDevScale, dword(d, i)));
 #pragma unroll
-        for (int i = 0; i < 5; ++i) B.g[i * Q + o] = sr_half((g[i] - ge[i]) * kDevScale, dword(d, 9 + i));
+        for (int i = 0; i < 5; ++i) __stwb(B.g + i * Q + o, sr_half((g[i] - ge[i]) * kDevScale, dword(d, 9 + i)));
     }
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
@@ -1014,7 +1016,7 @@ struct StoreH16NT {
         r.y = *reinterpret_cast<const unsigned int*>(&b0);
         r.z = *reinterpret_cast<const unsigned int*>(&a1);
         r.w = *reinterpret_cast<const unsigned int*>(&b1);
-        *reinterpret_cast<uint4*>(B.rec + o) = r;
+        __stwb(reinterpret_cast<uint4*>(B.rec + o), r);
         const float2 fa0 = __half22float2(a0), fb0 = __half22float2(b0);
         const float2 fa1 = __half22float2(a1), fb1 = __half22float2(b1);
         const f2 br = f2(1.0) + f2::make(fa0.x, fa1.x), bX = f2::make(fa0.y, fa1.y), bY = f2::make(fb0.x, fb1.x);
@@ -1030,12 +1032,12 @@ struct StoreH16NT {
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const f2 d = (f[i] - fe[i]) * f2(kDevScale);
-            *reinterpret_cast<__half2*>(B.f + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, i));
+            __stwb(reinterpret_cast<__half2*>(B.f + i * Q + o), sr_half2(d.lo(), d.hi(), dword(rw, i)));
         }
 #pragma unroll
         for (int i = 0; i < 5; ++i) {
             const f2 d = (g[i] - ge[i]) * f2(kDevScale);
-            *reinterpret_cast<__half2*>(B.g + i * Q + o) = sr_half2(d.lo(), d.hi(), dword(rw, 9 + i));
+            __stwb(reinterpret_cast<__half2*>(B.g + i * Q + o), sr_half2(d.lo(), d.hi(), dword(rw, 9 + i)));
         }
     }
 };
@@ -1166,7 +1168,7 @@ template <class L, typename S>
 __device__ __forceinline__ uint32_t step_seq(const BufT<S>& in, const BufT<S>& out, int x, int y) {
     if (!in.seq) return 0U;
     const uint32_t seq = L::ld(in.seq);
-    if (x == 0 && y == 0) *out.seq = seq + 1U;
+    if (x == 0 && y == 0) __stwb(out.seq, seq + 1U);
     return seq;
 }
 
