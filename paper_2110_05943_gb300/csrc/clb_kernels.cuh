@@ -675,7 +675,10 @@ template <class L>
 struct StoreF64T {
     using Ld = L;
     static constexpr bool kCentred = false;   // g and T carried as they are
-    static constexpr bool kReload = true;     // interior f re-read before the update (see step_node)
+#ifndef CLB_F64_RELOAD
+#define CLB_F64_RELOAD 1
+#endif
+    static constexpr bool kReload = CLB_F64_RELOAD != 0;   // interior f re-read before the update (see step_interior)
     using R = double;
     using S = double;
     static __device__ __forceinline__ void pull9(const BufT<const S>& B, const AuxT<R>&, const KParamsT<R>& K, int x,
