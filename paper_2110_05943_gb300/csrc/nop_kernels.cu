@@ -12,8 +12,10 @@
 //   forward : Y[p, co]   = sum_{tap, ci} X[p + d(tap), ci] W[tap, ci, co] (+ b, ReLU)
 //   dgrad   : dX[p, ci]  = sum_{tap, co} dY[p - d(tap), co] W[tap, ci, co]
 //   wgrad   : dW[tap, ci, co] += sum_p X[p + d(tap), ci] dY[p, co]   (split K, FP32 atomics)
+#include <cuda.h>           // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
 #include <stdint.h>
 
 #include <algorithm>
@@ -450,6 +452,221 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __nv_bfloat16* __r
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+
+// ---------------------------------------------------------------- TMA + tcgen05
+// Forward and input-gradient convolutions with operands fetched by the Tensor
+// Memory Accelerator.  A tile is 128 pixels = whole image rows (wbox x hbox,
+// wbox * hbox = 128).  The K loop runs over (tap, 64-channel chunk): per
+// iteration one 4-D TMA load brings the activations of the tile shifted by the
+// tap -- (c0 .. c0 + 63, w0 + dx, h0 + dy, image) -- and the hardware fills
+// everything outside the tensor with zeros, which is exactly the convolution's
+// zero padding (and pads a chunk past the last channel); one 3-D TMA load
+// brings the matching weights, tile_n rows of 64 channels.  Both land in
+// shared memory as 128-byte rows with the 128-byte swizzle, the K-major
+// layout tcgen05.mma reads (K = 16 per MMA: the descriptor start advances 32
+// bytes).  A ring of `stages` buffers: thread 0 issues the loads (each stage's
+// mbarrier expects the bytes of both boxes), thread 32 issues four MMAs per
+// stage and commits them to the stage's "empty" mbarrier, which frees it for
+// the next load.  Every wait is bounded; on expiry the CTA waits (bounded) for
+// the loads it issued, skips its output, frees its TMEM and sets the flag.
+constexpr int TM_K = 64;                         // channels per K step: one 128-byte row
+constexpr int TM_A_BYTES = TC_M * TM_K * 2;      // 16 KB per A stage
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
+                                            int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Bounded wait with mbarrier.try_wait (the hardware may suspend the thread
+// between tries, so idle threads cost little issue bandwidth).
+__device__ __forceinline__ bool mbar_wait_try(uint32_t a, uint32_t parity, long long limit) {
+    const long long t0 = clock64();
+    while (true) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.u32 %0, 1, 0, P;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (clock64() - t0 > limit) return false;
+    }
+}
+
+// Shared-memory descriptor of a K-major operand stored as 128-byte rows with
+// the 128-byte swizzle: 8-row groups 1024 bytes apart (stride byte offset),
+// descriptor version 1, swizzle mode 2 (128-byte).
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+           (2ull << 61);
+}
+
+// MODE FWD: A = activations X (C = cin), B = W^T [cout][taps * cin] viewed as
+// (cin, taps, cout).  MODE DGRAD: A = output gradient dY (C = cout) at the
+// mirrored taps, B = W [taps * cin][cout] viewed as (cout, cin, taps).
+template <int MODE>
+__global__ void __launch_bounds__(TC_THREADS) k_conv_tma(const __grid_constant__ CUtensorMap mapA,
+                                                         const __grid_constant__ CUtensorMap mapB,
+                                                         const float* __restrict__ bias,
+                                                         const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
+                                                         int out_f32, int relu, ConvShape s, int M, int N, int tile_n,
+                                                         int tmem_cols, int vec_out, int stages, int cchunks) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* const smem =
+        smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // swizzled tiles start on 1024 B
+    const int b_bytes = tile_n * TM_K * 2;
+    const int stage_bytes = TM_A_BYTES + b_bytes;                        // a multiple of 1024 (tile_n % 16 == 0)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + stages * stage_bytes);
+    uint64_t* empty = full + stages;
+    uint64_t* done = empty + stages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * tile_n;
+    const int hw = s.h * s.w, img = m0 / hw, rem = m0 - img * hw, h0 = rem / s.w, w0 = rem - h0 * s.w;
+    const int sg = MODE == FWD ? 1 : -1;
+    const int niter = s.taps * cchunks;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < stages; ++i) {
+            mbar_init(smem_u32(&full[i]));
+            mbar_init(smem_u32(&empty[i]));
+        }
+        mbar_init(smem_u32(done));
+        s_issued = 0;
+        s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = true;
+    if (tid == 0) {   // producer
+        int it = 0;
+        for (; it < niter; ++it) {
+            const int st = it % stages;
+            if (it >= stages && !mbar_wait_try(smem_u32(&empty[st]), ((it / stages) - 1) & 1, TC_TIMEOUT_CYCLES)) {
+                ok = false;
+                break;
+            }
+            const int tap = it / cchunks, c0 = (it - tap * cchunks) * TM_K;
+            const int ddy = sg * tap_dy(tap, s.taps), ddx = sg * tap_dx(tap, s.taps);
+            const uint32_t fb = smem_u32(&full[st]), a_dst = smem_u32(smem + st * stage_bytes);
+            mbar_expect_tx(fb, (uint32_t)stage_bytes);
+            tma_load_4d(a_dst, &mapA, fb, c0, w0 + ddx, h0 + ddy, img);
+            if (MODE == FWD) tma_load_3d(a_dst + TM_A_BYTES, &mapB, fb, c0, tap, n0);
+            else tma_load_3d(a_dst + TM_A_BYTES, &mapB, fb, c0, n0, tap);
+        }
+        s_issued = it;
+    } else if (tid == 32) {   // MMA issuer
+        const uint32_t idesc = tc_idesc(tile_n);
+        int it = 0;
+        for (; it < niter; ++it) {
+            const int st = it % stages;
+            if (!mbar_wait_try(smem_u32(&full[st]), (it / stages) & 1, TC_TIMEOUT_CYCLES)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(smem + st * stage_bytes), b0 = a0 + TM_A_BYTES;
+#pragma unroll
+            for (int ks = 0; ks < TM_K / 16; ++ks)
+                tc_mma(tmem, tc_desc_sw128(a0 + ks * 32), tc_desc_sw128(b0 + ks * 32), idesc,
+                       (it > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(smem_u32(&empty[st]));
+        }
+        s_consumed = it;
+        tc_commit(smem_u32(done));   // arrives once every MMA issued above has completed
+    }
+    ok = ok && mbar_wait_try(smem_u32(done), 0u, TC_TIMEOUT_CYCLES);
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) {
+        // loads still in flight write this CTA's shared memory: wait for them (bounded)
+        for (int it = s_consumed; it < s_issued; ++it)
+            mbar_wait_try(smem_u32(&full[it % stages]), (it / stages) & 1, TC_TIMEOUT_CYCLES);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int nt = min(tile_n, N - n0);                 // live columns of this tile
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        for (int c0 = 0; c0 < tile_n; c0 += 8) {
+            uint32_t r[8];
+            tc_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+            if (row < M && c0 < nt) {
+                const int o = row * N + n0 + c0;
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    v[j] = __uint_as_float(r[j]);
+                    if (bias && c0 + j < nt) v[j] += bias[n0 + c0 + j];
+                    if (relu) v[j] = v[j] > 0.0f ? v[j] : 0.0f;
+                }
+                if (c0 + 8 <= nt && vec_out) {
+                    if (mask) {
+                        const uint4 mk = *reinterpret_cast<const uint4*>(mask + o);
+                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (!(__bfloat162float(mb[j]) > 0.0f)) v[j] = 0.0f;
+                    }
+                    if (out_f32) {
+                        float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+                        d[0] = make_float4(v[0], v[1], v[2], v[3]);
+                        d[1] = make_float4(v[4], v[5], v[6], v[7]);
+                    } else {
+                        uint4 pk;
+                        __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = pk;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (c0 + j >= nt) break;
+                        float x = v[j];
+                        if (mask && !(__bfloat162float(mask[o + j]) > 0.0f)) x = 0.0f;
+                        if (out_f32) reinterpret_cast<float*>(out)[o + j] = x;
+                        else reinterpret_cast<__nv_bfloat16*>(out)[o + j] = __float2bfloat16(x);
+                    }
+                }
+            }
+        }
+    } else if (tid == 0) {
+        atomicExch(&g_nop_timeout, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
 // Weight gradient on tcgen05: D[m = tap * cin + ci][n = co] = sum over pixels
 // p of X[p + d(tap)][ci] dY[p][co], K = pixels, split over gridDim.z CTAs
 // (FP32 atomics into dw).  Both operands are staged MN-major: a core matrix
@@ -593,6 +810,98 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// BF16 tensor map with 128-byte swizzle and zero fill outside the tensor;
+// dims[0] is the contiguous dimension, strides[i] the byte stride of dims[i + 1].
+bool encode_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
+                const cuuint32_t* box) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box,
+               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Launches the TMA-fed tcgen05 kernel; false when the shape is not one it
+// takes: tiles must be whole rows (width a multiple of 128, or a divisor of
+// 128 with the height a multiple of 128 / width), channel counts multiples
+// of 8 (16-byte strides), operands 16-byte aligned.
+template <int MODE>
+bool launch_tma(const void* A, const void* B, const float* bias, const void* mask, void* out, int out_f32, int relu,
+                ConvShape s, long long M, long long N, cudaStream_t st, int* rc) {
+    const int C = MODE == FWD ? s.cin : s.cout;
+    if (C % 8 || N % 8 || !aligned16(A) || !aligned16(B) || M <= 0 || N <= 0) return false;
+    if (s.taps != 9 && s.taps != 1) return false;
+    int wbox, hbox;
+    if (s.w >= TC_M) {
+        if (s.w % TC_M) return false;
+        wbox = TC_M;
+        hbox = 1;
+    } else {
+        if (TC_M % s.w || s.h % (TC_M / s.w)) return false;
+        wbox = s.w;
+        hbox = TC_M / s.w;
+    }
+    const long long npix = (long long)s.n * s.h * s.w;
+    const long long cmax = s.cin > s.cout ? s.cin : s.cout;
+    if (npix * cmax * s.taps >= 2147483647LL || M * N >= 2147483647LL) return false;
+    const int tile_n = N <= 256 ? (int)((N + 15) & ~15LL) : 256;
+    int cols = 32;
+    while (cols < tile_n) cols <<= 1;
+    const int stages = tile_n <= 128 ? 4 : 3;
+    const int cchunks = (C + TM_K - 1) / TM_K;
+    CUtensorMap ma, mb;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)s.w, (cuuint64_t)s.h, (cuuint64_t)s.n};
+        const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)s.w * C * 2, (cuuint64_t)s.h * s.w * C * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)TM_K, (cuuint32_t)wbox, (cuuint32_t)hbox, 1};
+        if (!encode_map(&ma, A, 4, dims, strides, box)) return false;
+    }
+    if (MODE == FWD) {   // W^T [cout][taps * cin] as (cin, taps, cout)
+        const cuuint64_t dims[3] = {(cuuint64_t)s.cin, (cuuint64_t)s.taps, (cuuint64_t)s.cout};
+        const cuuint64_t strides[2] = {(cuuint64_t)s.cin * 2, (cuuint64_t)s.taps * s.cin * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)TM_K, 1, (cuuint32_t)tile_n};
+        if (!encode_map(&mb, B, 3, dims, strides, box)) return false;
+    } else {             // W [taps * cin][cout] as (cout, cin, taps)
+        const cuuint64_t dims[3] = {(cuuint64_t)s.cout, (cuuint64_t)s.cin, (cuuint64_t)s.taps};
+        const cuuint64_t strides[2] = {(cuuint64_t)s.cout * 2, (cuuint64_t)s.cin * s.cout * 2};
+        const cuuint32_t box[3] = {(cuuint32_t)TM_K, (cuuint32_t)tile_n, 1};
+        if (!encode_map(&mb, B, 3, dims, strides, box)) return false;
+    }
+    const size_t stage_bytes = (size_t)TM_A_BYTES + (size_t)tile_n * TM_K * 2;
+    const size_t smem = 1024 + stages * stage_bytes + (2 * stages + 1) * 8 + 16;
+    if (cudaFuncSetAttribute(k_conv_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        *rc = CLB_NOP_ERR_CUDA;
+        return true;
+    }
+    const dim3 grid((unsigned)(M / TC_M), (unsigned)((N + tile_n - 1) / tile_n));
+    const int vec_out = N % 8 == 0 && aligned16(out) && (!mask || aligned16(mask));
+    k_conv_tma<MODE><<<grid, TC_THREADS, smem, st>>>(ma, mb, bias, (const __nv_bfloat16*)mask, out, out_f32, relu, s,
+                                                      (int)M, (int)N, tile_n, cols, vec_out, stages, cchunks);
+    *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+    return true;
+}
 
 // Launches the tcgen05 kernel; false when the shape is not one it takes.
 template <int MODE>
@@ -797,6 +1106,8 @@ extern "C" int clb_nop_conv_fwd(const void* x, const void* w, const void* wt, co
     const ConvShape s{n, h, wd, cin, cout, taps};
     const long long M = (long long)n * h * wd, K = (long long)taps * cin;
     int rc;
+    if (wt && launch_tma<FWD>(x, wt, bias, nullptr, y, y_f32, relu, s, M, cout, (cudaStream_t)stream, &rc))
+        return rc;
     if (wt && launch_tc<FWD>(x, wt, bias, nullptr, y, y_f32, relu, s, M, cout, K, (cudaStream_t)stream, &rc))
         return rc;
     return launch_gemm<FWD>(x, w, bias, nullptr, y, y_f32, relu, s, M, cout, K, 1, (cudaStream_t)stream);
@@ -808,6 +1119,7 @@ extern "C" int clb_nop_conv_dgrad(const void* dy, const void* w, const void* mas
     const ConvShape s{n, h, wd, cin, cout, taps};
     const long long M = (long long)n * h * wd, K = (long long)taps * cout;
     int rc;
+    if (launch_tma<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, (cudaStream_t)stream, &rc)) return rc;
     if (launch_tc<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, K, (cudaStream_t)stream, &rc)) return rc;
     return launch_gemm<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, K, 1, (cudaStream_t)stream);
 }

@@ -55,6 +55,15 @@ SHAPES = [  # n, h, w, cin, cout, taps: ragged against the 64 x 64 x 32 (mma.syn
     (1, 8, 8, 288, 96, 9),         # input gradient N = 288: two N tiles (256 + 32)
     (2, 10, 6, 24, 192, 9),
     (3, 16, 12, 48, 96, 9),
+    # whole-row tiles of 128 pixels: the TMA-fed path (channels zero-filled
+    # up to 64-wide chunks, image borders zero-filled by the loads)
+    (2, 8, 128, 24, 24, 9),        # W = 128, C = 24 < 64
+    (2, 8, 128, 8, 24, 9),         # the input layer's 8 channels
+    (1, 16, 64, 48, 96, 9),        # W = 64: tiles of 2 rows
+    (2, 16, 32, 96, 48, 9),        # W = 32, C = 96: two channel chunks
+    (2, 8, 128, 72, 24, 9),        # C = 72: 64 + 8
+    (1, 16, 16, 288, 96, 9),       # W = 16, C = 288; input gradient N = 288: two N tiles
+    (1, 8, 128, 24, 8, 1),         # 1x1 convolution
 ]
 # A production layer: the training batch (16 x 128^2), 24 -> 24 channels.
 PRODUCTION = (16, 128, 128, 24, 24, 9)
