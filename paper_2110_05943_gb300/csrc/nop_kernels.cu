@@ -455,22 +455,38 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __nv_bfloat16* __r
 
 // ---------------------------------------------------------------- TMA + tcgen05
 // Forward and input-gradient convolutions with operands fetched by the Tensor
-// Memory Accelerator.  A tile is 128 pixels = whole image rows (wbox x hbox,
-// wbox * hbox = 128).  The K loop runs over (tap, 64-channel chunk): per
-// iteration one 4-D TMA load brings the activations of the tile shifted by the
-// tap -- (c0 .. c0 + 63, w0 + dx, h0 + dy, image) -- and the hardware fills
-// everything outside the tensor with zeros, which is exactly the convolution's
-// zero padding (and pads a chunk past the last channel); one 3-D TMA load
-// brings the matching weights, tile_n rows of 64 channels.  Both land in
-// shared memory as 128-byte rows with the 128-byte swizzle, the K-major
-// layout tcgen05.mma reads (K = 16 per MMA: the descriptor start advances 32
-// bytes).  A ring of `stages` buffers: thread 0 issues the loads (each stage's
-// mbarrier expects the bytes of both boxes), thread 32 issues four MMAs per
-// stage and commits them to the stage's "empty" mbarrier, which frees it for
-// the next load.  Every wait is bounded; on expiry the CTA waits (bounded) for
-// the loads it issued, skips its output, frees its TMEM and sets the flag.
-constexpr int TM_K = 64;                         // channels per K step: one 128-byte row
-constexpr int TM_A_BYTES = TC_M * TM_K * 2;      // 16 KB per A stage
+// Memory Accelerator, in a persistent warp-specialised kernel.  A tile is 128
+// pixels = whole image rows (wbox x hbox, wbox * hbox = 128) by tile_n
+// outputs; each CTA walks the tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+// The K loop of a tile runs over (tap, kc-channel chunk), kc = 32 or 64: per
+// iteration one 4-D TMA load brings the activations of the tile shifted by
+// the tap -- (c0 .. c0 + kc - 1, w0 + dx, h0 + dy, image) -- and the hardware
+// fills everything outside the tensor with zeros, which is exactly the
+// convolution's zero padding (and pads a chunk past the last channel); one
+// 3-D TMA load brings the matching weights, tile_n rows of kc channels.  Both
+// land in shared memory as 2 kc-byte rows with the matching swizzle (64 or
+// 128 bytes), the K-major layout tcgen05.mma reads (K = 16 per MMA: the
+// descriptor start advances 32 bytes).
+//   warp 4 (one thread): producer -- a ring of `stages` buffers; each stage's
+//     "full" mbarrier expects the bytes of both boxes;
+//   warp 5 (one thread): MMA issuer -- kc / 16 MMAs per stage, committed to
+//     the stage's "empty" mbarrier; the tile's accumulator alternates between
+//     two TMEM buffers, committed to that buffer's "acc_full" mbarrier;
+//   warps 0-3: epilogue -- warp w reads TMEM lanes 32w .. 32w + 31 (one pixel
+//     per thread) of the finished buffer, adds the bias, applies ReLU or the
+//     mask, stores, and releases the buffer ("acc_empty", 128 arrivals), so
+//     the next tile's MMAs overlap this tile's epilogue.
+// Every wait is bounded; on expiry a role stops, the CTA waits (bounded) for
+// the loads and MMAs it issued, frees its TMEM and sets the flag.
+constexpr int TM_THREADS = 192;
+
+__device__ __forceinline__ void mbar_init_n(uint32_t a, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t a) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
 
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, uint32_t mbar, int c0, int c1,
                                             int c2, int c3) {
@@ -510,44 +526,96 @@ __device__ __forceinline__ bool mbar_wait_try(uint32_t a, uint32_t parity, long 
     }
 }
 
-// Shared-memory descriptor of a K-major operand stored as 128-byte rows with
-// the 128-byte swizzle: 8-row groups 1024 bytes apart (stride byte offset),
-// descriptor version 1, swizzle mode 2 (128-byte).
-__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t addr) {
-    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
-           (2ull << 61);
+// Shared-memory descriptor of a K-major operand stored as R-byte rows with
+// the R-byte swizzle (R = 128 or 64): 8-row groups 8R bytes apart (stride
+// byte offset), descriptor version 1, swizzle mode 2 (128-byte) or 4 (64-byte).
+__device__ __forceinline__ uint64_t tc_desc_sw(uint32_t addr, int row_bytes) {
+    const uint64_t mode = row_bytes == 128 ? 2ull : 4ull;
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)((8 * row_bytes) >> 4) << 32) |
+           (1ull << 46) | (mode << 61);
+}
+
+// Epilogue of one accumulator row (pixel `row`, outputs n0 .. n0 + nt - 1).
+__device__ __forceinline__ void tm_store_row(uint32_t taddr, int row, int n0, int nt, int tile_n, int N,
+                                             const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
+                                             void* __restrict__ out, int out_f32, int relu, int vec_out) {
+    for (int c0 = 0; c0 < tile_n; c0 += 8) {
+        uint32_t r[8];
+        tc_ld8(taddr + (uint32_t)c0, r);
+        if (c0 >= nt) continue;
+        const int o = row * N + n0 + c0;
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            v[j] = __uint_as_float(r[j]);
+            if (bias && c0 + j < nt) v[j] += bias[n0 + c0 + j];
+            if (relu) v[j] = v[j] > 0.0f ? v[j] : 0.0f;
+        }
+        if (c0 + 8 <= nt && vec_out) {
+            if (mask) {
+                const uint4 mk = *reinterpret_cast<const uint4*>(mask + o);
+                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    if (!(__bfloat162float(mb[j]) > 0.0f)) v[j] = 0.0f;
+            }
+            if (out_f32) {
+                float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+                d[0] = make_float4(v[0], v[1], v[2], v[3]);
+                d[1] = make_float4(v[4], v[5], v[6], v[7]);
+            } else {
+                uint4 pk;
+                __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = pk;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (c0 + j >= nt) break;
+                float x = v[j];
+                if (mask && !(__bfloat162float(mask[o + j]) > 0.0f)) x = 0.0f;
+                if (out_f32) reinterpret_cast<float*>(out)[o + j] = x;
+                else reinterpret_cast<__nv_bfloat16*>(out)[o + j] = __float2bfloat16(x);
+            }
+        }
+    }
 }
 
 // MODE FWD: A = activations X (C = cin), B = W^T [cout][taps * cin] viewed as
 // (cin, taps, cout).  MODE DGRAD: A = output gradient dY (C = cout) at the
 // mirrored taps, B = W [taps * cin][cout] viewed as (cout, cin, taps).
+// tmem_cols: columns of one accumulator buffer (two are allocated).
 template <int MODE>
-__global__ void __launch_bounds__(TC_THREADS) k_conv_tma(const __grid_constant__ CUtensorMap mapA,
+__global__ void __launch_bounds__(TM_THREADS, 1) k_conv_tma(const __grid_constant__ CUtensorMap mapA,
                                                          const __grid_constant__ CUtensorMap mapB,
                                                          const float* __restrict__ bias,
                                                          const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
                                                          int out_f32, int relu, ConvShape s, int M, int N, int tile_n,
-                                                         int tmem_cols, int vec_out, int stages, int cchunks) {
+                                                         int tmem_cols, int vec_out, int stages, int cchunks, int kc,
+                                                         int ntiles, int ntn) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char* const smem =
         smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // swizzled tiles start on 1024 B
-    const int b_bytes = tile_n * TM_K * 2;
-    const int stage_bytes = TM_A_BYTES + b_bytes;                        // a multiple of 1024 (tile_n % 16 == 0)
+    const int a_bytes = TC_M * kc * 2, b_bytes = tile_n * kc * 2;
+    const int stage_bytes = a_bytes + b_bytes;                           // a multiple of 1024 (tile_n % 16 == 0)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + stages * stage_bytes);
     uint64_t* empty = full + stages;
-    uint64_t* done = empty + stages;
+    uint64_t* acc_full = empty + stages;                                 // [2]
+    uint64_t* acc_empty = acc_full + 2;                                  // [2]
+    uint64_t* done = acc_empty + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     __shared__ int s_issued, s_consumed;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * tile_n;
-    const int hw = s.h * s.w, img = m0 / hw, rem = m0 - img * hw, h0 = rem / s.w, w0 = rem - h0 * s.w;
     const int sg = MODE == FWD ? 1 : -1;
     const int niter = s.taps * cchunks;
+    const int hw = s.h * s.w;
 
-    if (warp == 0) {
+    if (warp == 4) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
-                     "r"(tmem_cols)
+                     "r"(2 * tmem_cols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -555,6 +623,10 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tma(const __grid_constant__
         for (int i = 0; i < stages; ++i) {
             mbar_init(smem_u32(&full[i]));
             mbar_init(smem_u32(&empty[i]));
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&acc_full[b]));
+            mbar_init_n(smem_u32(&acc_empty[b]), 128);
         }
         mbar_init(smem_u32(done));
         s_issued = 0;
@@ -567,104 +639,97 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tma(const __grid_constant__
     const uint32_t tmem = *tmem_slot;
 
     bool ok = true;
-    if (tid == 0) {   // producer
-        int it = 0;
-        for (; it < niter; ++it) {
-            const int st = it % stages;
-            if (it >= stages && !mbar_wait_try(smem_u32(&empty[st]), ((it / stages) - 1) & 1, TC_TIMEOUT_CYCLES)) {
-                ok = false;
-                break;
+    if (warp == 4) {
+        if (lane == 0) {   // producer
+            int it = 0, st = 0, ph = 0;   // global iteration, its stage and the stage's use count parity
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int m0 = (t / ntn) * TC_M, n0 = (t % ntn) * tile_n;
+                const int img = m0 / hw, rem = m0 - img * hw, h0 = rem / s.w, w0 = rem - h0 * s.w;
+                for (int j = 0; j < niter; ++j) {
+                    if (it >= stages && !mbar_wait_try(smem_u32(&empty[st]), ph ^ 1, TC_TIMEOUT_CYCLES)) {
+                        ok = false;
+                        break;
+                    }
+                    const int tap = j / cchunks, c0 = (j - tap * cchunks) * kc;
+                    const int ddy = sg * tap_dy(tap, s.taps), ddx = sg * tap_dx(tap, s.taps);
+                    const uint32_t fb = smem_u32(&full[st]), a_dst = smem_u32(smem + st * stage_bytes);
+                    mbar_expect_tx(fb, (uint32_t)stage_bytes);
+                    tma_load_4d(a_dst, &mapA, fb, c0, w0 + ddx, h0 + ddy, img);
+                    if (MODE == FWD) tma_load_3d(a_dst + a_bytes, &mapB, fb, c0, tap, n0);
+                    else tma_load_3d(a_dst + a_bytes, &mapB, fb, c0, n0, tap);
+                    ++it;
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                }
             }
-            const int tap = it / cchunks, c0 = (it - tap * cchunks) * TM_K;
-            const int ddy = sg * tap_dy(tap, s.taps), ddx = sg * tap_dx(tap, s.taps);
-            const uint32_t fb = smem_u32(&full[st]), a_dst = smem_u32(smem + st * stage_bytes);
-            mbar_expect_tx(fb, (uint32_t)stage_bytes);
-            tma_load_4d(a_dst, &mapA, fb, c0, w0 + ddx, h0 + ddy, img);
-            if (MODE == FWD) tma_load_3d(a_dst + TM_A_BYTES, &mapB, fb, c0, tap, n0);
-            else tma_load_3d(a_dst + TM_A_BYTES, &mapB, fb, c0, n0, tap);
+            s_issued = it;
         }
-        s_issued = it;
-    } else if (tid == 32) {   // MMA issuer
-        const uint32_t idesc = tc_idesc(tile_n);
-        int it = 0;
-        for (; it < niter; ++it) {
-            const int st = it % stages;
-            if (!mbar_wait_try(smem_u32(&full[st]), (it / stages) & 1, TC_TIMEOUT_CYCLES)) {
+    } else if (warp == 5) {
+        if (lane == 0) {   // MMA issuer
+            const uint32_t idesc = tc_idesc(tile_n);
+            int it = 0, st = 0, ph = 0, lt = 0;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++lt) {
+                const int b = lt & 1;
+                if (lt >= 2 && !mbar_wait_try(smem_u32(&acc_empty[b]), ((lt >> 1) - 1) & 1, TC_TIMEOUT_CYCLES)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t d = tmem + (uint32_t)(b * tmem_cols);
+                for (int j = 0; j < niter; ++j) {
+                    if (!mbar_wait_try(smem_u32(&full[st]), ph, TC_TIMEOUT_CYCLES)) {
+                        ok = false;
+                        break;
+                    }
+                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                    const uint32_t a0 = smem_u32(smem + st * stage_bytes), b0 = a0 + a_bytes;
+                    for (int ks = 0; ks < kc / 16; ++ks)
+                        tc_mma(d, tc_desc_sw(a0 + ks * 32, 2 * kc), tc_desc_sw(b0 + ks * 32, 2 * kc), idesc,
+                               (j > 0 || ks > 0) ? 1u : 0u);
+                    tc_commit(smem_u32(&empty[st]));
+                    ++it;
+                    if (++st == stages) {
+                        st = 0;
+                        ph ^= 1;
+                    }
+                }
+                if (ok) tc_commit(smem_u32(&acc_full[b]));
+            }
+            s_consumed = it;
+            tc_commit(smem_u32(done));   // arrives once every MMA issued above has completed
+        }
+    } else {   // epilogue: warps 0-3
+        int lt = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            if (!mbar_wait_try(smem_u32(&acc_full[b]), (lt >> 1) & 1, TC_TIMEOUT_CYCLES)) {
                 ok = false;
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a0 = smem_u32(smem + st * stage_bytes), b0 = a0 + TM_A_BYTES;
-#pragma unroll
-            for (int ks = 0; ks < TM_K / 16; ++ks)
-                tc_mma(tmem, tc_desc_sw128(a0 + ks * 32), tc_desc_sw128(b0 + ks * 32), idesc,
-                       (it > 0 || ks > 0) ? 1u : 0u);
-            tc_commit(smem_u32(&empty[st]));
+            const int m0 = (t / ntn) * TC_M, n0 = (t % ntn) * tile_n;
+            const int row = m0 + warp * 32 + lane;
+            tm_store_row(tmem + (uint32_t)(b * tmem_cols) + ((uint32_t)(warp * 32) << 16), row, n0,
+                         min(tile_n, N - n0), tile_n, N, bias, mask, out, out_f32, relu, vec_out);
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            mbar_arrive(smem_u32(&acc_empty[b]));
         }
-        s_consumed = it;
-        tc_commit(smem_u32(done));   // arrives once every MMA issued above has completed
     }
-    ok = ok && mbar_wait_try(smem_u32(done), 0u, TC_TIMEOUT_CYCLES);
+    if (tid == 160) ok = mbar_wait_try(smem_u32(done), 0u, TC_TIMEOUT_CYCLES) && ok;
     ok = __syncthreads_and(ok);
-    if (!ok && tid == 0) {
+    if (!ok && tid == 128) {
         // loads still in flight write this CTA's shared memory: wait for them (bounded)
         for (int it = s_consumed; it < s_issued; ++it)
             mbar_wait_try(smem_u32(&full[it % stages]), (it / stages) & 1, TC_TIMEOUT_CYCLES);
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int nt = min(tile_n, N - n0);                 // live columns of this tile
-    if (ok) {
-        const int row = m0 + warp * 32 + lane;
-        for (int c0 = 0; c0 < tile_n; c0 += 8) {
-            uint32_t r[8];
-            tc_ld8(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-            if (row < M && c0 < nt) {
-                const int o = row * N + n0 + c0;
-                float v[8];
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    v[j] = __uint_as_float(r[j]);
-                    if (bias && c0 + j < nt) v[j] += bias[n0 + c0 + j];
-                    if (relu) v[j] = v[j] > 0.0f ? v[j] : 0.0f;
-                }
-                if (c0 + 8 <= nt && vec_out) {
-                    if (mask) {
-                        const uint4 mk = *reinterpret_cast<const uint4*>(mask + o);
-                        const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
-#pragma unroll
-                        for (int j = 0; j < 8; ++j)
-                            if (!(__bfloat162float(mb[j]) > 0.0f)) v[j] = 0.0f;
-                    }
-                    if (out_f32) {
-                        float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
-                        d[0] = make_float4(v[0], v[1], v[2], v[3]);
-                        d[1] = make_float4(v[4], v[5], v[6], v[7]);
-                    } else {
-                        uint4 pk;
-                        __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
-#pragma unroll
-                        for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                        *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = pk;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        if (c0 + j >= nt) break;
-                        float x = v[j];
-                        if (mask && !(__bfloat162float(mask[o + j]) > 0.0f)) x = 0.0f;
-                        if (out_f32) reinterpret_cast<float*>(out)[o + j] = x;
-                        else reinterpret_cast<__nv_bfloat16*>(out)[o + j] = __float2bfloat16(x);
-                    }
-                }
-            }
-        }
-    } else if (tid == 0) {
         atomicExch(&g_nop_timeout, 1u);
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    if (warp == 4)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * tmem_cols)
+                     : "memory");
 }
 
 // Weight gradient on tcgen05: D[m = tap * cin + ci][n = co] = sum over pixels
@@ -811,6 +876,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
+// Streaming multiprocessors of the current device (looked up once).
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) ==
+                                                      cudaSuccess && v > 0)
+            n = v;
+        else
+            n = 148;
+    }
+    return n;
+}
+
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime
 // (no link-time dependency on libcuda).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -830,15 +909,15 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// BF16 tensor map with 128-byte swizzle and zero fill outside the tensor;
+// BF16 tensor map with the given swizzle and zero fill outside the tensor;
 // dims[0] is the contiguous dimension, strides[i] the byte stride of dims[i + 1].
 bool encode_map(CUtensorMap* map, const void* base, int rank, const cuuint64_t* dims, const cuuint64_t* strides,
-                const cuuint32_t* box) {
+                const cuuint32_t* box, CUtensorMapSwizzle swizzle) {
     PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
     if (!enc) return false;
     const cuuint32_t ones[4] = {1, 1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box,
-               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -868,37 +947,47 @@ bool launch_tma(const void* A, const void* B, const float* bias, const void* mas
     const int tile_n = N <= 256 ? (int)((N + 15) & ~15LL) : 256;
     int cols = 32;
     while (cols < tile_n) cols <<= 1;
-    const int stages = tile_n <= 128 ? 4 : 3;
-    const int cchunks = (C + TM_K - 1) / TM_K;
+    // 32-channel chunks (64-byte rows) when they waste fewer zero-filled channels
+    const int kc = (C < 128 && (C + 31) / 32 * 32 < (C + 63) / 64 * 64) ? 32 : 64;
+    const int cchunks = (C + kc - 1) / kc;
+    // two CTAs per SM (two accumulator buffers each) while both fit in TMEM
+    const int per_sm = 2 * cols <= 256 ? 2 : 1;
+    const size_t stage_bytes = (size_t)TC_M * kc * 2 + (size_t)tile_n * kc * 2;
+    const size_t budget = (per_sm == 2 ? 110 : 220) * 1024 - 1024 - 128;
+    const int stages = (int)std::min<size_t>(8, budget / stage_bytes);
+    if (stages < 2) return false;
     CUtensorMap ma, mb;
+    const CUtensorMapSwizzle sw = kc == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
     {
         const cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)s.w, (cuuint64_t)s.h, (cuuint64_t)s.n};
         const cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)s.w * C * 2, (cuuint64_t)s.h * s.w * C * 2};
-        const cuuint32_t box[4] = {(cuuint32_t)TM_K, (cuuint32_t)wbox, (cuuint32_t)hbox, 1};
-        if (!encode_map(&ma, A, 4, dims, strides, box)) return false;
+        const cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)wbox, (cuuint32_t)hbox, 1};
+        if (!encode_map(&ma, A, 4, dims, strides, box, sw)) return false;
     }
     if (MODE == FWD) {   // W^T [cout][taps * cin] as (cin, taps, cout)
         const cuuint64_t dims[3] = {(cuuint64_t)s.cin, (cuuint64_t)s.taps, (cuuint64_t)s.cout};
         const cuuint64_t strides[2] = {(cuuint64_t)s.cin * 2, (cuuint64_t)s.taps * s.cin * 2};
-        const cuuint32_t box[3] = {(cuuint32_t)TM_K, 1, (cuuint32_t)tile_n};
-        if (!encode_map(&mb, B, 3, dims, strides, box)) return false;
+        const cuuint32_t box[3] = {(cuuint32_t)kc, 1, (cuuint32_t)tile_n};
+        if (!encode_map(&mb, B, 3, dims, strides, box, sw)) return false;
     } else {             // W [taps * cin][cout] as (cout, cin, taps)
         const cuuint64_t dims[3] = {(cuuint64_t)s.cout, (cuuint64_t)s.cin, (cuuint64_t)s.taps};
         const cuuint64_t strides[2] = {(cuuint64_t)s.cout * 2, (cuuint64_t)s.cin * s.cout * 2};
-        const cuuint32_t box[3] = {(cuuint32_t)TM_K, (cuuint32_t)tile_n, 1};
-        if (!encode_map(&mb, B, 3, dims, strides, box)) return false;
+        const cuuint32_t box[3] = {(cuuint32_t)kc, (cuuint32_t)tile_n, 1};
+        if (!encode_map(&mb, B, 3, dims, strides, box, sw)) return false;
     }
-    const size_t stage_bytes = (size_t)TM_A_BYTES + (size_t)tile_n * TM_K * 2;
-    const size_t smem = 1024 + stages * stage_bytes + (2 * stages + 1) * 8 + 16;
+    const size_t smem = 1024 + stages * stage_bytes + (2 * stages + 5) * 8 + 16;
     if (cudaFuncSetAttribute(k_conv_tma<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         *rc = CLB_NOP_ERR_CUDA;
         return true;
     }
-    const dim3 grid((unsigned)(M / TC_M), (unsigned)((N + tile_n - 1) / tile_n));
+    const int ntn = (int)((N + tile_n - 1) / tile_n);
+    const long long ntiles = (M / TC_M) * ntn;
+    const unsigned grid = (unsigned)std::min<long long>(ntiles, (long long)sm_count() * per_sm);
     const int vec_out = N % 8 == 0 && aligned16(out) && (!mask || aligned16(mask));
-    k_conv_tma<MODE><<<grid, TC_THREADS, smem, st>>>(ma, mb, bias, (const __nv_bfloat16*)mask, out, out_f32, relu, s,
-                                                      (int)M, (int)N, tile_n, cols, vec_out, stages, cchunks);
+    k_conv_tma<MODE><<<grid, TM_THREADS, smem, st>>>(ma, mb, bias, (const __nv_bfloat16*)mask, out, out_f32, relu, s,
+                                                      (int)M, (int)N, tile_n, cols, vec_out, stages, cchunks, kc,
+                                                      (int)ntiles, ntn);
     *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
     return true;
 }
@@ -1094,6 +1183,235 @@ __global__ void k_cast_bf16(const float* __restrict__ x, __nv_bfloat16* __restri
 
 unsigned nblk(long long n) { return (unsigned)((n + 255) / 256); }
 
+// ------------------------------------------------ 16-byte (8-channel) forms
+// The same operations, one uint4 of eight BF16 channels per thread, taken
+// when every channel count is a multiple of 8 and every pointer is 16-byte
+// aligned (all layers of the network); the scalar kernels above stay for the
+// other shapes.
+__device__ __forceinline__ void unpack8(const uint4 v, float (&f)[8]) {
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float2 t = __bfloat1622float2(h[j]);
+        f[2 * j] = t.x;
+        f[2 * j + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 pack8(const float (&f)[8]) {
+    uint4 v;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&v);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) h[j] = __floats2bfloat162_rn(f[2 * j], f[2 * j + 1]);
+    return v;
+}
+
+// n * h * w pixels of G = c / 8 vectors; vector index i -> (pixel, group)
+__global__ void k_pool2_fwd8(const uint4* __restrict__ x, uint4* __restrict__ y, int n, int h, int w, int G) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ho = h / 2, wo = w / 2;
+    if (i >= (long long)n * ho * wo * G) return;
+    const int g = (int)(i % G);
+    long long p = i / G;
+    const int xo = (int)(p % wo);
+    p /= wo;
+    const int yo = (int)(p % ho);
+    const int b = (int)(p / ho);
+    const long long base = (((long long)b * h + 2 * yo) * w + 2 * xo) * G + g;
+    float a[8], t[8];
+    unpack8(x[base], a);
+    unpack8(x[base + G], t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += t[j];
+    unpack8(x[base + (long long)w * G], t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += t[j];
+    unpack8(x[base + (long long)w * G + G], t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] = 0.25f * (a[j] + t[j]);
+    y[i] = pack8(a);
+}
+
+__global__ void k_pool2_bwd8(const uint4* __restrict__ dy, uint4* __restrict__ dx, int n, int h, int w, int G) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * h * w * G) return;
+    const int g = (int)(i % G);
+    long long p = i / G;
+    const int x = (int)(p % w);
+    p /= w;
+    const int y = (int)(p % h);
+    const int b = (int)(p / h);
+    float a[8];
+    unpack8(dy[(((long long)b * (h / 2) + y / 2) * (w / 2) + x / 2) * G + g], a);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] *= 0.25f;
+    dx[i] = pack8(a);
+}
+
+__global__ void k_up2_fwd8(const uint4* __restrict__ x, uint4* __restrict__ y, int n, int h, int w, int G) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int H = 2 * h, W = 2 * w;
+    if (i >= (long long)n * H * W * G) return;
+    const int g = (int)(i % G);
+    long long p = i / G;
+    const int X = (int)(p % W);
+    p /= W;
+    const int Y = (int)(p % H);
+    const int b = (int)(p / H);
+    y[i] = x[(((long long)b * h + Y / 2) * w + X / 2) * G + g];
+}
+
+__global__ void k_up2_bwd8(const uint4* __restrict__ dy, uint4* __restrict__ dx, int n, int h, int w, int G) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (long long)n * h * w * G) return;
+    const int g = (int)(i % G);
+    long long p = i / G;
+    const int x = (int)(p % w);
+    p /= w;
+    const int y = (int)(p % h);
+    const int b = (int)(p / h);
+    const int W = 2 * w;
+    const long long base = (((long long)b * 2 * h + 2 * y) * W + 2 * x) * G + g;
+    float a[8], t[8];
+    unpack8(dy[base], a);
+    unpack8(dy[base + G], t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += t[j];
+    unpack8(dy[base + (long long)W * G], t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += t[j];
+    unpack8(dy[base + (long long)W * G + G], t);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) a[j] += t[j];
+    dx[i] = pack8(a);
+}
+
+// ga = ca / 8 and gb = cb / 8 vectors per pixel
+__global__ void k_concat8(uint4* __restrict__ a, uint4* __restrict__ b, uint4* __restrict__ y, long long npix, int ga,
+                          int gb, int inverse) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int G = ga + gb;
+    if (i >= npix * G) return;
+    const long long p = i / G;
+    const int g = (int)(i - p * G);
+    uint4* src = g < ga ? a + p * ga + g : b + p * gb + (g - ga);
+    if (!inverse) y[i] = *src;
+    else *src = y[i];
+}
+
+__global__ void k_add_mask8(const uint4* __restrict__ d1, const uint4* __restrict__ d2, const uint4* __restrict__ a,
+                            uint4* __restrict__ out, long long n8) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n8) return;
+    float v[8], t[8];
+    unpack8(d1[i], v);
+    if (d2) {
+        unpack8(d2[i], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] += t[j];
+    }
+    if (a) {
+        unpack8(a[i], t);
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (!(t[j] > 0.0f)) v[j] = 0.0f;
+    }
+    out[i] = pack8(v);
+}
+
+// Bias gradient db[ch] += sum_p dy[p][ch] for c % 8 == 0: a grid-stride loop
+// over 16-byte vectors with a stride that is a multiple of G = c / 8, so every
+// thread keeps one channel group; per-block sums of the threads of each group
+// (shared memory), then one FP32 atomic per block and channel.
+constexpr int BG_THREADS = 256;
+constexpr int BG_BLOCKS = 2 * 152;
+
+__global__ void __launch_bounds__(BG_THREADS) k_bias_grad8(const uint4* __restrict__ dy, float* __restrict__ db,
+                                                            long long n8, int G) {
+    __shared__ float part[BG_THREADS][9];
+    const int T = (BG_THREADS / G) * G;              // threads in use: a multiple of G
+    const int t = threadIdx.x;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (t < T) {
+        const long long stride = (long long)T * gridDim.x;
+        for (long long i = (long long)blockIdx.x * T + t; i < n8; i += stride) {
+            float v[8];
+            unpack8(dy[i], v);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) s[j] += v[j];
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) part[t][j] = s[j];
+    __syncthreads();
+    // thread (g, j) of the first 8 G sums lane j of group g over the block's threads t = g (mod G)
+    for (int q = t; q < 8 * G; q += BG_THREADS) {
+        const int g = q >> 3, j = q & 7;
+        float acc = 0.0f;
+        for (int u = g; u < T; u += G) acc += part[u][j];
+        atomicAdd(db + 8 * g + j, acc);
+    }
+}
+
+// Weight gradient of a 1x1 convolution with few outputs (the network's head):
+// dw[ci][co] += sum_p x[p][ci] dy[p][co] for CIN inputs (a multiple of 8) and
+// COUT outputs; each thread accumulates all CIN * COUT products over a strided
+// set of pixels, then warp shuffles and one atomic per block and weight.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_wgrad_small(const __nv_bfloat16* __restrict__ x,
+                                                     const __nv_bfloat16* __restrict__ dy, float* __restrict__ dw,
+                                                     long long npix) {
+    __shared__ float red[8][CIN * COUT];
+    float acc[CIN * COUT];
+#pragma unroll
+    for (int k = 0; k < CIN * COUT; ++k) acc[k] = 0.0f;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
+         p += (long long)blockDim.x * gridDim.x) {
+        float d[COUT];
+#pragma unroll
+        for (int o = 0; o < COUT; ++o) d[o] = __bfloat162float(dy[p * COUT + o]);
+        const uint4* xr = reinterpret_cast<const uint4*>(x + p * CIN);
+#pragma unroll
+        for (int v = 0; v < CIN / 8; ++v) {
+            float xv[8];
+            unpack8(xr[v], xv);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+#pragma unroll
+                for (int o = 0; o < COUT; ++o) acc[(8 * v + j) * COUT + o] = fmaf(xv[j], d[o], acc[(8 * v + j) * COUT + o]);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < CIN * COUT; ++k) {
+        float v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) red[warp][k] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < CIN * COUT; k += blockDim.x) {
+        float v = 0.0f;
+        for (int wi = 0; wi < 8; ++wi) v += red[wi][k];
+        atomicAdd(dw + k, v);
+    }
+}
+
+// Launches k_wgrad_small for the shapes it is instantiated for; false otherwise.
+bool launch_wgrad_small(const void* x, const void* dy, float* dw, ConvShape s, cudaStream_t st, int* rc) {
+    if (s.taps != 1 || !aligned16(x)) return false;
+    const long long npix = (long long)s.n * s.h * s.w;
+    const unsigned grid = (unsigned)std::min<long long>(4 * 152, (npix + 255) / 256);
+    const __nv_bfloat16 *xb = (const __nv_bfloat16*)x, *db = (const __nv_bfloat16*)dy;
+    if (s.cout == 4 && s.cin == 8) k_wgrad_small<8, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
+    else if (s.cout == 4 && s.cin == 16) k_wgrad_small<16, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
+    else if (s.cout == 4 && s.cin == 24) k_wgrad_small<24, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
+    else if (s.cout == 4 && s.cin == 32) k_wgrad_small<32, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
+    else return false;
+    *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+    return true;
+}
+
 int status() { return cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA; }
 
 }  // namespace
@@ -1130,12 +1448,19 @@ extern "C" int clb_nop_conv_wgrad(const void* x, const void* dy, float* dw, int3
     const ConvShape s{n, h, wd, cin, cout, taps};
     int rc;
     if (launch_wgrad_tc(x, dy, dw, s, splitk, (cudaStream_t)stream, &rc)) return rc;
+    if (launch_wgrad_small(x, dy, dw, s, (cudaStream_t)stream, &rc)) return rc;
     return launch_gemm<WGRAD>(x, dy, nullptr, nullptr, dw, 1, 0, s, (long long)taps * cin, cout, (long long)n * h * wd,
                               splitk, (cudaStream_t)stream);
 }
 
 extern "C" int clb_nop_bias_grad(const void* dy, float* db, int64_t npix, int32_t c, void* stream) {
     if (!dy || !db || npix < 1 || c < 1) return CLB_NOP_ERR_ARG;
+    if (c % 8 == 0 && c / 8 <= BG_THREADS && aligned16(dy)) {
+        const long long n8 = npix * (c / 8);
+        const unsigned grid = (unsigned)std::min<long long>(BG_BLOCKS, (n8 + BG_THREADS - 1) / BG_THREADS);
+        k_bias_grad8<<<grid, BG_THREADS, 0, (cudaStream_t)stream>>>((const uint4*)dy, db, n8, c / 8);
+        return status();
+    }
     k_bias_grad<<<(unsigned)((npix + 255) / 256), 128, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)dy, db, npix, c);
     return status();
 }
@@ -1144,6 +1469,15 @@ extern "C" int clb_nop_pool2(const void* in, void* out, int32_t n, int32_t h, in
                              void* stream) {
     if (!in || !out || n < 1 || h < 2 || w < 2 || c < 1 || (h & 1) || (w & 1)) return CLB_NOP_ERR_ARG;
     const cudaStream_t st = (cudaStream_t)stream;
+    if (c % 8 == 0 && aligned16(in) && aligned16(out)) {
+        const int G = c / 8;
+        if (!backward)
+            k_pool2_fwd8<<<nblk((long long)n * (h / 2) * (w / 2) * G), 256, 0, st>>>((const uint4*)in, (uint4*)out, n, h,
+                                                                                    w, G);
+        else
+            k_pool2_bwd8<<<nblk((long long)n * h * w * G), 256, 0, st>>>((const uint4*)in, (uint4*)out, n, h, w, G);
+        return status();
+    }
     if (!backward)
         k_pool2_fwd<<<nblk((long long)n * (h / 2) * (w / 2) * c), 256, 0, st>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, n, h, w, c);
     else
@@ -1155,6 +1489,14 @@ extern "C" int clb_nop_up2(const void* in, void* out, int32_t n, int32_t h, int3
                            void* stream) {
     if (!in || !out || n < 1 || h < 1 || w < 1 || c < 1) return CLB_NOP_ERR_ARG;
     const cudaStream_t st = (cudaStream_t)stream;
+    if (c % 8 == 0 && aligned16(in) && aligned16(out)) {
+        const int G = c / 8;
+        if (!backward)
+            k_up2_fwd8<<<nblk((long long)n * 4 * h * w * G), 256, 0, st>>>((const uint4*)in, (uint4*)out, n, h, w, G);
+        else
+            k_up2_bwd8<<<nblk((long long)n * h * w * G), 256, 0, st>>>((const uint4*)in, (uint4*)out, n, h, w, G);
+        return status();
+    }
     if (!backward)
         k_up2_fwd<<<nblk((long long)n * 4 * h * w * c), 256, 0, st>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, n, h, w, c);
     else
@@ -1165,6 +1507,11 @@ extern "C" int clb_nop_up2(const void* in, void* out, int32_t n, int32_t h, int3
 extern "C" int clb_nop_concat(void* a, void* b, void* y, int64_t npix, int32_t ca, int32_t cb, int32_t inverse,
                               void* stream) {
     if (!a || !b || !y || npix < 1 || ca < 1 || cb < 1) return CLB_NOP_ERR_ARG;
+    if (ca % 8 == 0 && cb % 8 == 0 && aligned16(a) && aligned16(b) && aligned16(y)) {
+        k_concat8<<<nblk(npix * ((ca + cb) / 8)), 256, 0, (cudaStream_t)stream>>>((uint4*)a, (uint4*)b, (uint4*)y, npix,
+                                                                                  ca / 8, cb / 8, inverse);
+        return status();
+    }
     k_concat<<<nblk(npix * (ca + cb)), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)a, (const __nv_bfloat16*)b,
                                                                         (__nv_bfloat16*)y, npix, ca, cb, inverse);
     return status();
@@ -1216,6 +1563,11 @@ __global__ void k_add_mask(const __nv_bfloat16* __restrict__ d1, const __nv_bflo
 
 extern "C" int clb_nop_add_mask(const void* d1, const void* d2, const void* a, void* out, int64_t n, void* stream) {
     if (!d1 || !out || n < 1) return CLB_NOP_ERR_ARG;
+    if (n % 8 == 0 && aligned16(d1) && aligned16(out) && (!d2 || aligned16(d2)) && (!a || aligned16(a))) {
+        k_add_mask8<<<nblk(n / 8), 256, 0, (cudaStream_t)stream>>>((const uint4*)d1, (const uint4*)d2,
+                                                                   (const uint4*)a, (uint4*)out, n / 8);
+        return status();
+    }
     k_add_mask<<<nblk(n), 256, 0, (cudaStream_t)stream>>>((const __nv_bfloat16*)d1, (const __nv_bfloat16*)d2,
                                                           (const __nv_bfloat16*)a, (__nv_bfloat16*)out, n);
     return status();

@@ -107,7 +107,12 @@ def test_conv_input_gradient(lib, shape):
     _close(dx.cpu(), ref, 8e-3)
 
 
-@pytest.mark.parametrize("shape,splitk", [(s, k) for s in SHAPES for k in (1, 7)] + [(PRODUCTION, 0)])
+# the network's head (1x1, 24 -> 4) on its own CUDA-core kernel, small and at the training batch
+HEADS = [(2, 8, 12, 24, 4, 1), (3, 5, 7, 8, 4, 1), (16, 128, 128, 24, 4, 1)]
+
+
+@pytest.mark.parametrize("shape,splitk", [(s, k) for s in SHAPES for k in (1, 7)] + [(PRODUCTION, 0)] +
+                         [(s, 0) for s in HEADS])
 def test_conv_weight_gradient(lib, shape, splitk):
     """splitk 0 = the library's own split, as training calls it: on the
     production layer a single FP32 tensor-core accumulator over all 262,144
@@ -128,8 +133,10 @@ def test_transpose(lib):
     assert torch.equal(wt.cpu(), w.t())
 
 
-def test_bias_grad_pool_up_concat(lib):
-    n, h, w, c = 2, 10, 14, 12
+@pytest.mark.parametrize("c,ca,cb,nadd", [(12, 5, 9, 1001), (24, 48, 24, 1000), (288, 96, 192, 4096)])
+def test_bias_grad_pool_up_concat(lib, c, ca, cb, nadd):
+    """c, ca, cb, nadd multiples of 8: the 16-byte (8-channel) kernels; otherwise the scalar ones."""
+    n, h, w = 2, 10, 14
     dy = _bf((n, h, w, c), 10)
     db = torch.zeros(c, device="cuda")
     assert lib.clb_nop_bias_grad(_p(dy.cuda()), _p(db), n * h * w, c, None) == 0
@@ -159,19 +166,30 @@ def test_bias_grad_pool_up_concat(lib):
     assert lib.clb_nop_up2(_p(gu.cuda()), _p(ds), n, h, w, c, 1, None) == 0
     _close(ds.cpu(), sr.grad, 8e-3)
 
-    a, b = _bf((n * h * w, 5), 15), _bf((n * h * w, 9), 16)
-    yy = torch.empty((n * h * w, 14), device="cuda", dtype=torch.bfloat16)
+    a, b = _bf((n * h * w, ca), 15), _bf((n * h * w, cb), 16)
+    yy = torch.empty((n * h * w, ca + cb), device="cuda", dtype=torch.bfloat16)
     ad, bd = a.cuda(), b.cuda()
-    assert lib.clb_nop_concat(_p(ad), _p(bd), _p(yy), n * h * w, 5, 9, 0, None) == 0
+    assert lib.clb_nop_concat(_p(ad), _p(bd), _p(yy), n * h * w, ca, cb, 0, None) == 0
     assert torch.equal(yy.cpu(), torch.cat([a, b], dim=1))
     a2, b2 = torch.empty_like(ad), torch.empty_like(bd)
-    assert lib.clb_nop_concat(_p(a2), _p(b2), _p(yy), n * h * w, 5, 9, 1, None) == 0
+    assert lib.clb_nop_concat(_p(a2), _p(b2), _p(yy), n * h * w, ca, cb, 1, None) == 0
     assert torch.equal(a2.cpu(), a) and torch.equal(b2.cpu(), b)
 
-    d1, d2, m = _bf((1000,), 17), _bf((1000,), 18), _bf((1000,), 19)
-    out = torch.empty((1000,), device="cuda", dtype=torch.bfloat16)
-    assert lib.clb_nop_add_mask(_p(d1.cuda()), _p(d2.cuda()), _p(m.cuda()), _p(out), 1000, None) == 0
+    d1, d2, m = _bf((nadd,), 17), _bf((nadd,), 18), _bf((nadd,), 19)
+    out = torch.empty((nadd,), device="cuda", dtype=torch.bfloat16)
+    assert lib.clb_nop_add_mask(_p(d1.cuda()), _p(d2.cuda()), _p(m.cuda()), _p(out), nadd, None) == 0
     _close(out.cpu(), (d1.float() + d2.float()) * (m.float() > 0), 8e-3)
+    assert lib.clb_nop_add_mask(_p(d1.cuda()), None, _p(m.cuda()), _p(out), nadd, None) == 0
+    _close(out.cpu(), d1.float() * (m.float() > 0), 8e-3)
+
+
+def test_bias_grad_production(lib):
+    """The training batch's 128^2 x 16 images, 24 channels (grid-stride vector sums)."""
+    npix, c = 16 * 128 * 128, 24
+    dy = _bf((npix, c), 21)
+    db = torch.zeros(c, device="cuda")
+    assert lib.clb_nop_bias_grad(_p(dy.cuda()), _p(db), npix, c, None) == 0
+    _close(db.cpu(), dy.double().sum(dim=0).float(), 1e-5)
 
 
 def test_mse_and_adam(lib):
