@@ -546,10 +546,10 @@ CLB_HD void collide5(R (&g)[5], R n0, R T, R X, R Y, const PhysT<R>& P) {
 // a = zeta_a, b = 1 - 2 (1 - zeta_a) with the shift and 1 without it.
 template <int I, typename R>
 CLB_HD R geqc_comp(R Tt, R X, R Y, R sigma, R cT2, R T0) {
-    const R T = Tt + T0;
-    if (I == 0) return fma(Tt, sigma - R(2) * cT2, -T * fma(X, X, Y * Y));
+    if (I == 0) return fma(Tt, sigma - R(2) * cT2, -(Tt + T0) * fma(X, X, Y * Y));
     const R u = (I == 1 || I == 3) ? X : Y;
-    return R(0.5) * fma(Tt, cT2, T * (u * (u + R((I == 1 || I == 2) ? 1.0 : -1.0))));
+    const R hT = fma(Tt, R(0.5), R(0.5) * T0);     // T / 2
+    return fma(Tt, R(0.5) * cT2, hT * (u * (u + R((I == 1 || I == 2) ? 1.0 : -1.0))));
 }
 
 template <typename R>
@@ -587,20 +587,7 @@ __device__ __forceinline__ R sum5(const R (&v)[5]) {
     return ((v[0] + v[1]) + (v[2] + v[3])) + v[4];
 }
 
-// Packing of per-node constants and model parameters for the paired path.
-__device__ __forceinline__ CoefT<f2> pack_coef(const CoefT<float>& a, const CoefT<float>& b) {
-    CoefT<f2> c;
-    c.ip = f2::make(a.ip, b.ip);
-    c.l0 = f2::make(a.l0, b.l0);
-    c.l0sq = f2::make(a.l0sq, b.l0sq);
-    c.aux = f2::make(a.aux, b.aux);
-    c.hdar = f2::make(a.hdar, b.hdar);
-    c.hgx = f2::make(a.hgx, b.hgx);
-    c.hgb = f2::make(a.hgb, b.hgb);
-    c.hgy = f2::make(a.hgy, b.hgy);
-    return c;
-}
-
+// Model parameters for the paired path.
 __device__ __forceinline__ PhysT<f2> splat(const PhysT<float>& p) {
     PhysT<f2> q;
     q.ax = f2(p.ax);
@@ -723,7 +710,11 @@ struct StoreF64T {
     }
 };
 
-using StoreF64 = StoreF64T<LdNC>;
+// Loader of the stand-alone FP64 step's distribution buffers.
+#ifndef CLB_F64_LD
+#define CLB_F64_LD LdNC
+#endif
+using StoreF64 = StoreF64T<CLB_F64_LD>;
 
 // FP32 constants of a node from its porosity and its row's a_y - g beta T0
 // (Eqs. 4, 5, 23).
@@ -740,6 +731,23 @@ __device__ __forceinline__ CoefT<float> coef_from_phi(float p, float ip, float a
     c.hgx = hp * K.p.ax;
     c.hgb = hp * K.p.gbeta;
     c.hgy = hp * ayg;
+    return c;
+}
+
+// The same constants for a pair of nodes on packed FP32 (bit for bit the
+// values of coef_from_phi: the same operations lane by lane).
+template <bool FORCH>
+__device__ __forceinline__ CoefT<f2> coef2_from_phi(f2 p, f2 ip, float ayg, const KParamsT<float>& K) {
+    CoefT<f2> c;
+    const f2 hp = f2(0.5) * p;
+    c.ip = ip;
+    c.hdar = hp * f2(K.nuK);
+    c.l0 = fma(f2(0.5), c.hdar, f2(0.5));
+    c.l0sq = c.l0 * c.l0;
+    c.aux = FORCH ? f2(K.l1c) * f2::make(rsqrtf(p.lo()), rsqrtf(p.hi())) : recip(c.l0 + c.l0);
+    c.hgx = hp * f2(K.p.ax);
+    c.hgb = hp * f2(K.p.gbeta);
+    c.hgy = hp * f2(ayg);
     return c;
 }
 
@@ -786,6 +794,12 @@ struct StoreH16T {
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
         const float p = __ldg(A.phi + y * K.g.nx + x);
         return coef_from_phi<FORCH>(p, recip(p), A.ayg[y], K);
+    }
+    template <bool FORCH>
+    static __device__ __forceinline__ CoefT<f2> coef2(const AuxT<R>& A, const KParamsT<R>& K, int x0, int y) {
+        const float* q = A.phi + y * K.g.nx + x0;
+        const f2 p = f2::make(__ldg(q), __ldg(q + 1));
+        return coef2_from_phi<FORCH>(p, recip(p), A.ayg[y], K);
     }
     // Two interior nodes (x0, x0 + 1), x0 even, neither at the periodic x
     // seam: node x0 + 1 pulls from the offsets of node x0 plus one.
@@ -852,28 +866,37 @@ __device__ __forceinline__ Base load_base(const BufT<const __half>& B, const Aux
 }
 
 // One component of the porous equilibrium f^eq = M^-1 m^eq (Eq. 19), written
-// out per direction (the value a puller needs from each source):
-//   f0 = rho (4/9) - (2/3) A (X^2 + Y^2) + A ip X^2 Y^2,                 A = rho / phi
-//   f1,3 = (1/2)[ (2/9) rho +- (2/3) rho X + A ((2/3) X^2 - Y^2 / 3 -+ X Y^2) - A ip X^2 Y^2 ]
-//   f2,4 = the same with X <-> Y
-//   f5..8 = (1/4)[ rho / 9 + (rho / 3)(sx X + sy Y) + A ((X^2 + Y^2) / 3 + sx sy X Y + sy X^2 Y + sx X Y^2)
-//                  + A ip X^2 Y^2 ],  (sx, sy) = e_i
+// out per direction (the value a puller needs from each source).  With
+// A = rho / phi, S = X^2 + Y^2 and, for direction e_i, the signed velocity
+// components a = e_ix X, b = e_iy Y:
+//   f0       = (4/9) rho + A (ip X^2 Y^2 - (2/3) S)
+//   f1..4    = rho (1/9 + d/3) - (A/2) (o^2 (1/3 + d + ip d^2) - (2/3) d^2),
+//              d = the signed component along e_i, o the other one
+//   f5..8    = rho (1/36 + s/12) + (A/4) (S/3 + ab (1 + s) + ip (XY)^2),  s = a + b
+// (the cubic and quartic terms of Eq. 19 grouped so that the direction's
+// signs only ever select constants or an addition against a subtraction:
+// the packed type has no free negation).
 template <int I, typename R>
 __device__ __forceinline__ R feq_comp(R rho, R X, R Y, R ip) {
-    const R A = rho * ip, X2 = X * X, Y2 = Y * Y, Q = A * ip * X2 * Y2;
-    if (I == 0) return fma(rho, R(4.0 / 9.0), fma(R(-2.0 / 3.0) * A, X2 + Y2, Q));
-    if (I == 1 || I == 3) {
-        const R t = fma(R(2.0 / 3.0), X2, fma(R(-1.0 / 3.0), Y2, R(I == 1 ? -1.0 : 1.0) * X * Y2));
-        return R(0.5) * (fma(rho, fma(R(I == 1 ? 2.0 / 3.0 : -2.0 / 3.0), X, R(2.0 / 9.0)), fma(A, t, -Q)));
+    if (I == 0) {
+        const R X2 = X * X, Y2 = Y * Y;
+        return fma(rho * ip, fma(ip * X2, Y2, R(-2.0 / 3.0) * (X2 + Y2)), rho * R(4.0 / 9.0));
+    } else if (I <= 4) {
+        constexpr bool pos = I <= 2;                                   // e_i along +x or +y
+        const R u = (I == 1 || I == 3) ? X : Y, o = (I == 1 || I == 3) ? Y : X;
+        const R d2 = u * u;
+        const R w = fma(ip, d2, pos ? u + R(1.0 / 3.0) : R(1.0 / 3.0) - u);   // 1/3 + d + ip d^2
+        const R tn = fma(o * o, w, R(-2.0 / 3.0) * d2);
+        return fma(rho * (R(-0.5) * ip), tn, rho * fma(u, R(pos ? 1.0 / 3.0 : -1.0 / 3.0), R(1.0 / 9.0)));
+    } else {
+        // s holds a + b, except for I = 7 (a + b = -(X + Y)), where it holds X + Y
+        const R XY = X * Y;
+        const R s = I == 5 || I == 7 ? X + Y : (I == 6 ? Y - X : X - Y);
+        // ab (1 + a + b) = XY c:  c = 1 + s (I = 5), 1 - s (I = 7), -1 - s (I = 6, 8)
+        const R c = I == 5 ? s + R(1.0) : (I == 7 ? R(1.0) - s : R(-1.0) - s);
+        const R t = fma(R(1.0 / 3.0), fma(X, X, Y * Y), fma(XY, c, (ip * XY) * XY));
+        return fma(rho * (R(0.25) * ip), t, rho * fma(s, R(I == 7 ? -1.0 / 12.0 : 1.0 / 12.0), R(1.0 / 36.0)));
     }
-    if (I == 2 || I == 4) {
-        const R t = fma(R(2.0 / 3.0), Y2, fma(R(-1.0 / 3.0), X2, R(I == 2 ? -1.0 : 1.0) * Y * X2));
-        return R(0.5) * (fma(rho, fma(R(I == 2 ? 2.0 / 3.0 : -2.0 / 3.0), Y, R(2.0 / 9.0)), fma(A, t, -Q)));
-    }
-    const double sx = (I == 5 || I == 8) ? 1.0 : -1.0, sy = (I == 5 || I == 6) ? 1.0 : -1.0;
-    const R XY = X * Y;
-    const R t = fma(R(1.0 / 3.0), X2 + Y2, fma(R(sx * sy), XY, XY * fma(R(sy), X, R(sx) * Y)));
-    return R(0.25) * (fma(rho, fma(R(1.0 / 3.0), fma(R(sx), X, R(sy) * Y), R(1.0 / 9.0)), fma(A, t, Q)));
 }
 
 template <int I, class L>
@@ -955,6 +978,12 @@ struct StoreH16NT {
     static __device__ __forceinline__ CoefT<R> coef(const AuxT<R>& A, const KParamsT<R>& K, int x, int y) {
         const float ip = __ldg(A.ip + y * K.g.px + x);
         return coef_from_phi<FORCH>(recip(ip), ip, A.ayg[y], K);
+    }
+    template <bool FORCH>
+    static __device__ __forceinline__ CoefT<f2> coef2(const AuxT<R>& A, const KParamsT<R>& K, int x0, int y) {
+        const float2 q = __ldg(reinterpret_cast<const float2*>(A.ip + y * K.g.px + x0));   // x0 and px even
+        const f2 ip = f2::make(q.x, q.y);
+        return coef2_from_phi<FORCH>(recip(ip), ip, A.ayg[y], K);
     }
     // Two interior nodes (x0, x0 + 1), x0 even, neither at the periodic x
     // seam (node x0 + 1 pulls from node x0's offsets plus one).
@@ -1305,7 +1334,7 @@ template <class P, bool SHIFT, bool FORCH>
 __device__ __forceinline__ void step_pair_interior(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
                                                    const AuxT<float>& A, const KParamsT<float>& K, int x0, int y) {
     const PhysT<f2> P2 = splat(K.p);
-    const CoefT<f2> c = pack_coef(P::template coef<FORCH>(A, K, x0, y), P::template coef<FORCH>(A, K, x0 + 1, y));
+    const CoefT<f2> c = P::template coef2<FORCH>(A, K, x0, y);
     f2 f[9], g[5];
     P::pull2(as_const(in), A, K, x0, y, f, g);
     const Mom9T<f2> k = moments9(f);
@@ -1450,9 +1479,14 @@ __device__ __forceinline__ void batch_tiles(const CaseT<typename P::R, typename 
     }
 }
 
+// Resident 128-thread blocks per SM the batch kernels are compiled for.
+#ifndef CLB_BATCH_MINB
+#define CLB_BATCH_MINB 4
+#endif
+
 // One step per launch: block b owns tiles [b * per_cta, (b + 1) * per_cta).
 template <class P, int NPT, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(128, 4) k_step_batch(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
+__global__ void __launch_bounds__(128, CLB_BATCH_MINB) k_step_batch(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
                                                        const int4* __restrict__ tiles, int ntiles, int per_cta,
                                                        int par) {
     __shared__ __align__(16) unsigned char raw[sizeof(CaseT<typename P::R, typename P::S>)];
@@ -1516,7 +1550,7 @@ __device__ __forceinline__ bool grid_barrier(GridBarrier* bar, int step, int ext
 // that gives up sets bar->failed and every block returns; the host reports
 // CLB_ERR_TIMEOUT.
 template <class P, int NPT, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(128, 4)
+__global__ void __launch_bounds__(128, CLB_BATCH_MINB)
     k_step_batch_persist(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
                          const int4* __restrict__ tiles, int ntiles, int chunk, int par0, int nsteps,
                          GridBarrier* bar, int extra, long long limit) {
