@@ -193,8 +193,30 @@ size_t clb_state_bytes(const clb_handle* h);
 int clb_get_state(clb_handle* h, void* buf, size_t bytes);
 int clb_set_state(clb_handle* h, const void* buf, size_t bytes);
 
-/* Wait for all work issued on the handle's stream. */
+/* Wait for all work issued on the handle's stream.  Returns CLB_ERR_TIMEOUT
+ * (once; the flag is cleared) if a bounded wait of the TMA-fed FP16N step
+ * expired since the last check -- the state is then invalid.  clb_macros and
+ * clb_nusselt report the same. */
 int clb_sync(clb_handle* h);
+
+/* FP16N form: the interior rows (1 .. ny - 2) of each step run a persistent
+ * kernel fed by bulk tensor copies (TMA) into shared memory, the edge nodes
+ * the per-thread kernel; the two paths give the same bits (the collision of
+ * Eqs. 11-18 and 28-34 is the same code, only the loads differ).  This
+ * selects the path: enable = 1 (available for FP16N with ny >= 3 and a
+ * driver that encodes the tensor maps) or 0 (the default: the step is bound
+ * by its arithmetic, and the per-thread kernel measured faster).
+ * CLB_ERR_ARG when enabling it is not possible.  Drops the captured step
+ * graphs. */
+int clb_set_tma(clb_handle* h, int32_t enable);
+
+/* Failure-path check of the TMA-fed step: runs one step of it into the idle
+ * buffer (time and state unchanged) in which every CTA's first wait is on a
+ * barrier that nothing completes, bounded by limit_cycles (>= 1) SM clock
+ * cycles; a CTA whose wait expired waits for its own copies (with the normal
+ * bound) before it exits.  Then reports like clb_sync: CLB_ERR_TIMEOUT when
+ * the expiry was detected and reported (the expected result). */
+int clb_tma_selftest(clb_handle* h, int64_t limit_cycles);
 
 void clb_destroy(clb_handle* h);
 

@@ -119,7 +119,9 @@ def load(build_if_needed: bool = True):
                  "clb_batch_barrier_selftest"):
         getattr(L, name).restype = ctypes.c_int
     L.clb_fp64_special_check.argtypes = [_VP, ctypes.c_int64, _VP, _VP]
-    for name in ("clb_fp64_special_check", "clb_nusselt_field_static", "clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
+    L.clb_set_tma.argtypes = [_VP, ctypes.c_int32]
+    L.clb_tma_selftest.argtypes = [_VP, ctypes.c_int64]
+    for name in ("clb_set_tma", "clb_tma_selftest", "clb_fp64_special_check", "clb_nusselt_field_static", "clb_init", "clb_step", "clb_set_fields", "clb_macros", "clb_macros_device", "clb_nusselt",
                  "clb_residual", "clb_lattice_params", "clb_get_state", "clb_set_state", "clb_sync"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
@@ -271,6 +273,16 @@ def clb_sync(h):
     _check(load().clb_sync(h), h)
 
 
+def clb_set_tma(h, enable: bool):
+    _check(load().clb_set_tma(h, int(bool(enable))), h)
+
+
+def clb_tma_selftest(h, limit_cycles: int) -> int:
+    """Status of the TMA-fed step's expiry check (CLB_ERR_TIMEOUT expected,
+    see clb.h); the simulation's state is unchanged."""
+    return load().clb_tma_selftest(h, int(limit_cycles))
+
+
 def clb_destroy(h):
     if h:
         load().clb_destroy(h)
@@ -322,6 +334,9 @@ class Simulation:
 
     def sync(self):
         clb_sync(self.handle)
+
+    def set_tma(self, enable: bool):
+        clb_set_tma(self.handle, enable)
 
     def close(self):
         if self.handle:

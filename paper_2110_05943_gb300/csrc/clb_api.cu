@@ -4,7 +4,9 @@
 // device memory for the two storage forms (FP64, and FP16 deviations from
 // the rest state with FP32 arithmetic), the CUDA-graph step driver, and the
 // FP64 reductions for the Nusselt number and the steady-state residual.
+#include <cuda.h>             // CUtensorMap (the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>     // PFN_cuTensorMapEncodeTiled
 
 #include <algorithm>
 #include <cmath>
@@ -14,12 +16,14 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <string>
 #include <vector>
 
 #include "../../include/clb.h"
 #include "clb_kernels.cuh"
 #include "clb_reduce.cuh"
+#include "clb_tma.cuh"
 
 using namespace clb;
 
@@ -68,6 +72,12 @@ struct clb_handle {
     bool graph_failed = false;
     dim3 block, grid;          // one node per thread
     dim3 block2, grid2;        // two nodes per thread (FP16 forms)
+    // FP16N form: tensor maps of the TMA-fed interior (per input buffer: f
+    // planes, g planes, records; and 1/phi), its tiling, and the wait bound
+    CUtensorMap tm_f[2], tm_g[2], tm_r[2], tm_i;
+    bool tma_avail = false, tma = false;
+    int tma_tiles_x = 0, tma_ntiles = 0, tma_grid = 0;
+    unsigned* tma_fail = nullptr;   // device flag set by a CTA whose wait expired
     std::string err;
 
     AuxT<double> aux64() const { return AuxT<double>{coef, nullptr, nullptr, (const double*)ayg}; }
@@ -216,6 +226,77 @@ static void pick_launch(clb_handle* h) {
     shape_blocks((nx + 1) / 2, ny, 16, 128, h->block2, h->grid2);
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link-time dependency on libcuda).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// Non-swizzled tensor map with zero fill outside the tensor; dims[0] is the
+// contiguous dimension, strides[i] the byte stride of dims[i + 1].
+static bool encode_map(CUtensorMap* m, CUtensorMapDataType type, const void* base, int rank, const cuuint64_t* dims,
+                       const cuuint64_t* strides, const cuuint32_t* box) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint32_t ones[3] = {1, 1, 1};
+    return enc(m, type, (cuuint32_t)rank, const_cast<void*>(base), dims, strides, box, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Tensor maps and tiling of the TMA-fed FP16N interior (rows 1 .. ny - 2 in
+// tiles of TT_X x TT_Y nodes); false leaves the plain k_step2 path in use.
+static bool setup_tma(clb_handle* h) {
+    const Geo& G = h->k32.g;
+    if (h->prec != CLB_F16N || G.ny < 3 || !h->tma_fail) return false;
+    const cuuint64_t px = (cuuint64_t)G.px, ny = (cuuint64_t)G.ny;
+    for (int b = 0; b < 2; ++b) {
+        const cuuint64_t df[3] = {px, ny, 9}, dg[3] = {px, ny, 5};
+        const cuuint64_t sp[2] = {px * 2, (cuuint64_t)G.plane * 2};
+        const cuuint32_t bp[3] = {(cuuint32_t)TT_FX, (cuuint32_t)TT_Y, 1};
+        const cuuint64_t dr[2] = {px, ny}, sr[1] = {px * 8};
+        const cuuint32_t br[2] = {(cuuint32_t)TT_RX, (cuuint32_t)(TT_Y + 2)};
+        if (!encode_map(&h->tm_f[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, h->f[b], 3, df, sp, bp) ||
+            !encode_map(&h->tm_g[b], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, h->g[b], 3, dg, sp, bp) ||
+            !encode_map(&h->tm_r[b], CU_TENSOR_MAP_DATA_TYPE_UINT64, h->rec[b], 2, dr, sr, br))
+            return false;
+    }
+    const cuuint64_t di[2] = {px, ny}, si[1] = {px * 4};
+    const cuuint32_t bi[2] = {(cuuint32_t)TT_IX, (cuuint32_t)(TT_Y + 2)};
+    if (!encode_map(&h->tm_i, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, h->phi32, 2, di, si, bi)) return false;
+    h->tma_tiles_x = (G.nx + TT_X - 1) / TT_X;
+    h->tma_ntiles = h->tma_tiles_x * ((G.ny - 2 + TT_Y - 1) / TT_Y);
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess || sms < 1)
+        return false;
+    h->tma_grid = std::min(h->tma_ntiles, CLB_TT_MINB * sms);   // resident CTAs per SM (launch bounds)
+    return h->tma_ntiles > 0;
+}
+
+// Reports (and clears) an expired wait of the TMA-fed interior.
+static int tma_status(clb_handle* h) {
+    if (!h->tma_avail) return CLB_OK;
+    unsigned v = 0;
+    CK(h, cudaMemcpy(&v, h->tma_fail, sizeof v, cudaMemcpyDeviceToHost));
+    if (!v) return CLB_OK;
+    CK(h, cudaMemset(h->tma_fail, 0, sizeof v));
+    return fail(h, CLB_ERR_TIMEOUT, "a wait for the tile copies of the FP16N step expired; the state is invalid");
+}
+
 static void free_all(clb_handle* h) {
     for (int i = 0; i < 2; ++i) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
@@ -253,20 +334,44 @@ static void step_as(clb_handle* h, cudaStream_t s, const AuxT<typename P::R>& A,
 
 // FP16 forms: two nodes per thread (k_step2), grid over node pairs.
 template <class P>
-static void step2_as(clb_handle* h, cudaStream_t s) {
+static void step2_as(clb_handle* h, cudaStream_t s, long long limit = TT_LIMIT, int selftest = 0) {
     using S = typename P::S;
     const BufT<S> in = h->buf<S>(h->par), out = h->buf<S>(1 - h->par);
     const AuxT<float> A = h->aux32();
     const bool sh = h->prm.shift != 0, fo = h->prm.forchheimer != 0;
-    // pair tiles (interior pairs only), then the edge nodes (see k_step2)
+    // pair tiles (interior pairs only), then the edge nodes (see k_step2);
+    // with the TMA-fed interior, the pair tiles cover only the rows 0 and
+    // ny - 1 of a periodic y
     const Geo& G = h->k32.g;
-    const int tx = (int)h->grid2.x, nt = (int)(h->grid2.x * h->grid2.y);
+    const int tx = (int)h->grid2.x;
+    int nt = (int)(h->grid2.x * h->grid2.y), outer = 0;
+    if constexpr (std::is_same<P, StoreH16N>::value) {
+        if (h->tma) {
+            const int b = h->par;
+            const dim3 gr((unsigned)h->tma_grid), bl(TT_THREADS);
+            if (sh && fo)
+                k_step2n_tma<true, true><<<gr, bl, TT_SMEM, s>>>(h->tm_f[b], h->tm_g[b], h->tm_r[b], h->tm_i, in, out, A,
+                                                                 h->k32, h->tma_tiles_x, h->tma_ntiles, limit, selftest, h->tma_fail);
+            else if (sh)
+                k_step2n_tma<true, false><<<gr, bl, TT_SMEM, s>>>(h->tm_f[b], h->tm_g[b], h->tm_r[b], h->tm_i, in, out, A,
+                                                                  h->k32, h->tma_tiles_x, h->tma_ntiles, limit, selftest, h->tma_fail);
+            else if (fo)
+                k_step2n_tma<false, true><<<gr, bl, TT_SMEM, s>>>(h->tm_f[b], h->tm_g[b], h->tm_r[b], h->tm_i, in, out, A,
+                                                                  h->k32, h->tma_tiles_x, h->tma_ntiles, limit, selftest, h->tma_fail);
+            else
+                k_step2n_tma<false, false><<<gr, bl, TT_SMEM, s>>>(h->tm_f[b], h->tm_g[b], h->tm_r[b], h->tm_i, in, out, A,
+                                                                   h->k32, h->tma_tiles_x, h->tma_ntiles, limit, selftest, h->tma_fail);
+            nt = G.wall_y ? 0 : tx;
+            outer = 1;
+        }
+    }
     const int threads = (int)(h->block2.x * h->block2.y);
     const unsigned nb = (unsigned)(nt + (edge_count(G) + threads - 1) / threads);
-    if (sh && fo) k_step2<P, true, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
-    else if (sh) k_step2<P, true, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
-    else if (fo) k_step2<P, false, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
-    else k_step2<P, false, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+    if (nb == 0) return;
+    if (sh && fo) k_step2<P, true, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
+    else if (sh) k_step2<P, true, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
+    else if (fo) k_step2<P, false, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
+    else k_step2<P, false, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
 }
 
 static void launch_step(clb_handle* h, cudaStream_t s) {
@@ -457,8 +562,10 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
     const size_t fbytes = (size_t)G.plane * 9 * h->es;
     const size_t gbytes = (size_t)G.plane * 5 * h->es;
     if (half) {
-        CKI(cudaMalloc(&h->seq, 2 * sizeof(unsigned)));
-        CKI(cudaMemsetAsync(h->seq, 0, 2 * sizeof(unsigned), h->stream));
+        // the two buffers' step counters and the TMA wait flag
+        CKI(cudaMalloc(&h->seq, 3 * sizeof(unsigned)));
+        CKI(cudaMemsetAsync(h->seq, 0, 3 * sizeof(unsigned), h->stream));
+        h->tma_fail = h->seq + 2;
     }
     for (int i = 0; i < 2; ++i) {
         CKI(cudaMalloc(&h->f[i], fbytes));
@@ -510,6 +617,10 @@ extern "C" int clb_init(clb_handle** out, const clb_params* p, const double* phi
     CKI(cudaGetLastError());
     int rc = set_fields_from_scratch(h);
     if (rc != CLB_OK) return bail(rc);
+    // available, off by default: the F16N step is bound by its arithmetic,
+    // not by load latency, and the per-thread kernel measured faster
+    h->tma_avail = setup_tma(h);
+    h->tma = false;
 #undef CKI
     *out = h;
     return CLB_OK;
@@ -596,6 +707,7 @@ extern "C" int clb_macros(clb_handle* h, double* rho, double* ux, double* uy, do
         if (outs[k])
             CK(h, cudaMemcpyAsync(outs[k], d + k * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (const int rc = tma_status(h)) return rc;
     for (int k = 0; k < 4; ++k)
         if (outs[k])
             for (long long i = 0; i < n; ++i)
@@ -621,6 +733,7 @@ extern "C" int clb_nusselt(clb_handle* h, int32_t side, double* nu) {
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpyAsync(h->host_res, h->result, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    if (const int rc = tma_status(h)) return rc;
     *nu = h->host_res[0];
     if (!std::isfinite(*nu)) return fail(h, CLB_ERR_UNSTABLE, "clb_nusselt: non-finite result");
     return CLB_OK;
@@ -725,7 +838,36 @@ extern "C" int clb_set_state(clb_handle* h, const void* buf, size_t bytes) {
 extern "C" int clb_sync(clb_handle* h) {
     if (!h) return CLB_ERR_ARG;
     CK(h, cudaStreamSynchronize(h->stream));
+    return tma_status(h);
+}
+
+extern "C" int clb_set_tma(clb_handle* h, int32_t enable) {
+    if (!h) return CLB_ERR_ARG;
+    if (enable && !h->tma_avail)
+        return fail(h, CLB_ERR_ARG, "clb_set_tma: the TMA-fed step is not available for this handle");
+    if ((enable != 0) != h->tma) {
+        // captured graphs hold the other path's launches
+        for (int i = 0; i < 2; ++i)
+            if (h->graph[i]) {
+                cudaGraphExecDestroy(h->graph[i]);
+                h->graph[i] = nullptr;
+            }
+        h->tma = enable != 0;
+    }
     return CLB_OK;
+}
+
+extern "C" int clb_tma_selftest(clb_handle* h, int64_t limit_cycles) {
+    if (!h || limit_cycles < 1) return CLB_ERR_ARG;
+    if (!h->tma_avail) return fail(h, CLB_ERR_ARG, "clb_tma_selftest: the TMA-fed step is not available");
+    CK(h, cudaStreamSynchronize(h->stream));
+    const bool save = h->tma;
+    h->tma = true;
+    step2_as<StoreH16N>(h, h->stream, (long long)limit_cycles, 1);   // writes the idle buffer; time and parity unchanged
+    h->tma = save;
+    CK(h, cudaGetLastError());
+    CK(h, cudaStreamSynchronize(h->stream));
+    return tma_status(h);
 }
 
 extern "C" void clb_destroy(clb_handle* h) {
