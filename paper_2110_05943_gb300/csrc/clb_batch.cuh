@@ -4,8 +4,10 @@
 // Each case is an ordinary clb_handle (its own buffers, parameters and
 // reductions); the batch builds a device table of the cases and a tile list
 // over the active ones and advances all of them, in one of two modes:
-//   CLB_BATCH_GRAPH      : one k_step_batch launch per step, replayed from
-//                          CUDA graphs of kGraphSteps steps;
+//   CLB_BATCH_GRAPH      : one k_step_batch launch per step (FP16 forms:
+//                          k_step_batch_int over the interior-pair tiles
+//                          and k_step_batch_edge over the edge nodes),
+//                          replayed from CUDA graphs of kGraphSteps steps;
 //   CLB_BATCH_PERSISTENT : one cooperative k_step_batch_persist launch per
 //                          kGraphSteps steps (itself captured in a graph),
 //                          its steps separated by a bounded grid barrier.
@@ -21,8 +23,12 @@ struct clb_batch {
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
     void* table = nullptr;          // CaseT array on the device
-    int4* tiles = nullptr;          // tile list on the device
+    int4* tiles = nullptr;          // tile list on the device (all tiles; FP64 and the persistent mode)
     int ntiles = 0;
+    int4* itiles = nullptr;         // FP16 forms, graph mode: interior-pair tiles (case, x0, y0)
+    int n_itiles = 0;
+    int4* echunks = nullptr;        // and chunks of edge nodes (case, first edge index, count)
+    int n_echunks = 0;
     int64_t nodes = 0;              // active nodes per step
     int par = 0;
     int64_t t = 0;
@@ -77,11 +83,26 @@ static void batch_drop_graphs(clb_batch* b) {
 
 static int nodes_per_thread(const clb_batch* b) { return b->prec == CLB_F64 ? 1 : 2; }
 
-// Tile list over the active cases for the current block shape.
+// Uploads a host list (replacing *dev).
+static int upload_list(clb_batch* b, const std::vector<int4>& host, int4** dev, int* n) {
+    cudaFree(*dev);
+    *dev = nullptr;
+    *n = (int)host.size();
+    if (*n) {
+        CKB(b, cudaMalloc(dev, host.size() * sizeof(int4)));
+        CKB(b, cudaMemcpy(*dev, host.data(), host.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    }
+    return CLB_OK;
+}
+
+// Tile lists over the active cases for the current block shape: all tiles
+// (FP64, persistent mode) and, for the FP16 forms, the interior-pair tiles
+// (pairs x0 = 2, 4, ... with x0 + 2 < nx, rows inside walled S/N sides) and
+// the edge nodes in chunks of up to 128 (the same split as k_step2).
 static int batch_build_tiles(clb_batch* b) {
     const int bx = kShapes[b->shape][0], by = kShapes[b->shape][1];
     const int tw = bx * nodes_per_thread(b);
-    std::vector<int4> host;
+    std::vector<int4> host, inner, edges;
     b->nodes = 0;
     for (size_t c = 0; c < b->cases.size(); ++c) {
         if (!b->active[c]) continue;
@@ -89,16 +110,20 @@ static int batch_build_tiles(clb_batch* b) {
         b->nodes += (int64_t)p.nx * p.ny;
         for (int y0 = 0; y0 < p.ny; y0 += by)
             for (int x0 = 0; x0 < p.nx; x0 += tw) host.push_back(make_int4((int)c, x0, y0, 0));
+        if (b->prec == CLB_F64) continue;
+        const Geo& G = b->cases[c]->k32.g;
+        const int y_lo = G.wall_y ? 1 : 0, y_hi = G.wall_y ? G.ny - 2 : G.ny - 1;
+        for (int y0 = y_lo; y0 <= y_hi; y0 += by)
+            for (int x0 = 2; x0 + 2 < G.nx; x0 += tw) inner.push_back(make_int4((int)c, x0, y0, 0));
+        const long long ne = edge_count(G);
+        for (long long i0 = 0; i0 < ne; i0 += 128)
+            edges.push_back(make_int4((int)c, (int)i0, (int)std::min(128LL, ne - i0), 0));
     }
-    cudaFree(b->tiles);
-    b->tiles = nullptr;
-    b->ntiles = (int)host.size();
-    if (b->ntiles) {
-        CKB(b, cudaMalloc(&b->tiles, host.size() * sizeof(int4)));
-        CKB(b, cudaMemcpy(b->tiles, host.data(), host.size() * sizeof(int4), cudaMemcpyHostToDevice));
-    }
+    int rc = upload_list(b, host, &b->tiles, &b->ntiles);
+    if (rc == CLB_OK) rc = upload_list(b, inner, &b->itiles, &b->n_itiles);
+    if (rc == CLB_OK) rc = upload_list(b, edges, &b->echunks, &b->n_echunks);
     batch_drop_graphs(b);
-    return CLB_OK;
+    return rc;
 }
 
 template <class P, int NPT>
@@ -106,11 +131,30 @@ static void batch_launch_as(clb_batch* b, cudaStream_t s) {
     using C = CaseT<typename P::R, typename P::S>;
     const C* tab = (const C*)b->table;
     const dim3 block(kShapes[b->shape][0], kShapes[b->shape][1]);
-    const int grid = (b->ntiles + b->per_cta - 1) / b->per_cta;
-    if (b->shift && b->forch) k_step_batch<P, NPT, true, true><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
-    else if (b->shift) k_step_batch<P, NPT, true, false><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
-    else if (b->forch) k_step_batch<P, NPT, false, true><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
-    else k_step_batch<P, NPT, false, false><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+    if constexpr (NPT == 2) {
+        if (b->n_itiles > 0) {
+            const int grid = (b->n_itiles + b->per_cta - 1) / b->per_cta;
+            const int4* t = b->itiles;
+            if (b->shift && b->forch) k_step_batch_int<P, true, true><<<grid, block, 0, s>>>(tab, t, b->n_itiles, b->per_cta, b->par);
+            else if (b->shift) k_step_batch_int<P, true, false><<<grid, block, 0, s>>>(tab, t, b->n_itiles, b->per_cta, b->par);
+            else if (b->forch) k_step_batch_int<P, false, true><<<grid, block, 0, s>>>(tab, t, b->n_itiles, b->per_cta, b->par);
+            else k_step_batch_int<P, false, false><<<grid, block, 0, s>>>(tab, t, b->n_itiles, b->per_cta, b->par);
+        }
+        if (b->n_echunks > 0) {
+            const int4* e = b->echunks;
+            const unsigned g = (unsigned)b->n_echunks;
+            if (b->shift && b->forch) k_step_batch_edge<P, true, true><<<g, 128, 0, s>>>(tab, e, b->par);
+            else if (b->shift) k_step_batch_edge<P, true, false><<<g, 128, 0, s>>>(tab, e, b->par);
+            else if (b->forch) k_step_batch_edge<P, false, true><<<g, 128, 0, s>>>(tab, e, b->par);
+            else k_step_batch_edge<P, false, false><<<g, 128, 0, s>>>(tab, e, b->par);
+        }
+    } else {
+        const int grid = (b->ntiles + b->per_cta - 1) / b->per_cta;
+        if (b->shift && b->forch) k_step_batch<P, NPT, true, true><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+        else if (b->shift) k_step_batch<P, NPT, true, false><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+        else if (b->forch) k_step_batch<P, NPT, false, true><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+        else k_step_batch<P, NPT, false, false><<<grid, block, 0, s>>>(tab, b->tiles, b->ntiles, b->per_cta, b->par);
+    }
 }
 
 // Persistent launch of `nsteps` steps from parity par0.  The grid is as
@@ -482,6 +526,8 @@ extern "C" void clb_batch_destroy(clb_batch* b) {
     cudaFree(b->bar);
     cudaFree(b->table);
     cudaFree(b->tiles);
+    cudaFree(b->itiles);
+    cudaFree(b->echunks);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
 }

@@ -715,11 +715,7 @@ struct StoreF64T {
     }
 };
 
-// Loader of the stand-alone FP64 step's distribution buffers.
-#ifndef CLB_F64_LD
-#define CLB_F64_LD LdNC
-#endif
-using StoreF64 = StoreF64T<CLB_F64_LD>;
+using StoreF64 = StoreF64T<LdNC>;
 
 // FP32 constants of a node from its porosity and its row's a_y - g beta T0
 // (Eqs. 4, 5, 23).
@@ -1523,6 +1519,65 @@ __global__ void __launch_bounds__(128, CLB_BATCH_MINB) k_step_batch(const CaseT<
     const int t0 = blockIdx.x * per_cta;
     int cur = -1;
     batch_tiles<P, NPT, SHIFT, FORCH>(cases, tiles, t0, min(t0 + per_cta, ntiles), par, raw, cur);
+}
+
+// Interior pair tiles of a batch (the FP16 forms, graph mode): `tiles` lists
+// (case, x0, y0) of tiles that lie in the interior-pair region of their case
+// (x0 >= 2, rows inside the walls), so every thread runs the packed interior
+// step and no thread carries the edge code; threads past the region's far
+// edges skip.  Edge nodes go to k_step_batch_edge.
+#ifndef CLB_BATCH_INT_MINB
+#define CLB_BATCH_INT_MINB 5
+#endif
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, CLB_BATCH_INT_MINB)
+    k_step_batch_int(const CaseT<typename P::R, typename P::S>* __restrict__ cases, const int4* __restrict__ tiles,
+                     int ntiles, int per_cta, int par) {
+    using C = CaseT<typename P::R, typename P::S>;
+    __shared__ __align__(16) unsigned char raw[sizeof(C)];
+    C& sc = *reinterpret_cast<C*>(raw);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    const int t0 = blockIdx.x * per_cta, t1 = min(t0 + per_cta, ntiles);
+    int cur = -1;
+    for (int t = t0; t < t1; ++t) {
+        const int4 tl = __ldg(tiles + t);
+        if (tl.x != cur) {
+            __syncthreads();
+            const unsigned* src = reinterpret_cast<const unsigned*>(cases + tl.x);
+            unsigned* dst = reinterpret_cast<unsigned*>(raw);
+            for (int w = tid; w < (int)(sizeof(C) / 4); w += nthr) dst[w] = __ldg(src + w);
+            __syncthreads();
+            cur = tl.x;
+        }
+        const int x0 = tl.y + 2 * threadIdx.x, y = tl.z + threadIdx.y;
+        const int y_hi = sc.K.g.wall_y ? sc.K.g.ny - 2 : sc.K.g.ny - 1;
+        if (x0 + 2 < sc.K.g.nx && y <= y_hi) {
+            const int b = par ^ sc.flip;
+            step_pair_interior<P, SHIFT, FORCH>(sc.b[b], sc.b[1 - b], sc.A, sc.K, x0, y);
+        }
+    }
+}
+
+// Edge nodes of a batch (the nodes k_step2 leaves to its per-node path):
+// `chunks` lists (case, first edge index, count) of at most blockDim nodes.
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, 4)
+    k_step_batch_edge(const CaseT<typename P::R, typename P::S>* __restrict__ cases, const int4* __restrict__ chunks,
+                      int par) {
+    using C = CaseT<typename P::R, typename P::S>;
+    __shared__ __align__(16) unsigned char raw[sizeof(C)];
+    C& sc = *reinterpret_cast<C*>(raw);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
+    const int4 ch = __ldg(chunks + blockIdx.x);
+    const unsigned* src = reinterpret_cast<const unsigned*>(cases + ch.x);
+    unsigned* dst = reinterpret_cast<unsigned*>(raw);
+    for (int w = tid; w < (int)(sizeof(C) / 4); w += nthr) dst[w] = __ldg(src + w);
+    __syncthreads();
+    if (tid >= ch.z) return;
+    int x, y;
+    edge_node(sc.K.g, (long long)ch.y + tid, x, y);
+    const int b = par ^ sc.flip;
+    step_node<P, SHIFT, FORCH>(sc.b[b], sc.b[1 - b], sc.A, sc.K, x, y);
 }
 
 // Grid barrier and work counters of the persistent batch launch, in device
