@@ -52,6 +52,13 @@ int clb_nop_conv_dgrad(const void* dy, const void* w, const void* mask, void* dx
 int clb_nop_conv_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t h, int32_t wd, int32_t cin,
                        int32_t cout, int32_t taps, int32_t splitk, void* stream);
 
+/* The weight gradient above and, in the same pass, the bias gradient
+ * db[co] += sum_{n,h,w} dy[n,h,w,co] (FP32; clear db first; db NULL: weights
+ * only).  On the tensor-core path the bias rides along as an extra row of
+ * ones in the pixel operand (when taps * cin is not a multiple of 128). */
+int clb_nop_conv_wgrad_bias(const void* x, const void* dy, float* dw, float* db, int32_t n, int32_t h, int32_t wd,
+                            int32_t cin, int32_t cout, int32_t taps, int32_t splitk, void* stream);
+
 /* db[c] += sum over npix pixels of dy[p][c]  (clear db first). */
 int clb_nop_bias_grad(const void* dy, float* db, int64_t npix, int32_t c, void* stream);
 
@@ -80,6 +87,26 @@ int clb_nop_mse(const float* pred, const float* target, const float* wch, int32_
  * FP32 gradient g and moments m, v; wb (BF16 copy of w) refreshed if not NULL. */
 int clb_nop_adam(float* w, const float* g, float* m, float* v, void* wb, int64_t n, float lr, float b1, float b2,
                  float eps, int32_t t, void* stream);
+
+/* One tensor of a multi-tensor Adam step: FP32 weights w, gradient g,
+ * moments m, v (n = rows * cols values, row-major [rows][cols]); wb (BF16
+ * copy, same layout) and wbt (BF16 transposed copy [cols][rows]) are
+ * refreshed when not NULL. */
+typedef struct {
+    float* w;
+    const float* g;
+    float* m;
+    float* v;
+    void* wb;
+    void* wbt;
+    int64_t n;
+    int32_t rows, cols;
+} clb_nop_adam_seg;
+
+/* The Adam step of clb_nop_adam on nseg tensors in one launch per 32 of them
+ * (segs: a host array, passed by value to the kernel). */
+int clb_nop_adam_multi(const clb_nop_adam_seg* segs, int32_t nseg, float lr, float b1, float b2, float eps, int32_t t,
+                       void* stream);
 
 /* out = (d1 + d2) where a > 0, else 0 (d2, a may be NULL: no term / no mask). */
 int clb_nop_add_mask(const void* d1, const void* d2, const void* a, void* out, int64_t n, void* stream);

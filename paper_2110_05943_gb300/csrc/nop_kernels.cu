@@ -479,6 +479,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv_tc(const __nv_bfloat16* __r
 // Every wait is bounded; on expiry a role stops, the CTA waits (bounded) for
 // the loads and MMAs it issued, frees its TMEM and sets the flag.
 constexpr int TM_THREADS = 192;
+constexpr int TM_BIAS_MAX = 1024;                // outputs whose bias is staged in shared memory
 
 __device__ __forceinline__ void mbar_init_n(uint32_t a, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
@@ -535,51 +536,84 @@ __device__ __forceinline__ uint64_t tc_desc_sw(uint32_t addr, int row_bytes) {
            (1ull << 46) | (mode << 61);
 }
 
-// Epilogue of one accumulator row (pixel `row`, outputs n0 .. n0 + nt - 1).
-__device__ __forceinline__ void tm_store_row(uint32_t taddr, int row, int n0, int nt, int tile_n, int N,
-                                             const float* __restrict__ bias, const __nv_bfloat16* __restrict__ mask,
-                                             void* __restrict__ out, int out_f32, int relu, int vec_out) {
-    for (int c0 = 0; c0 < tile_n; c0 += 8) {
-        uint32_t r[8];
-        tc_ld8(taddr + (uint32_t)c0, r);
-        if (c0 >= nt) continue;
-        const int o = row * N + n0 + c0;
-        float v[8];
+// 32 consecutive accumulator columns of this thread's TMEM lane (no wait).
+__device__ __forceinline__ void tc_ld32_nowait(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Epilogue of 8 accumulator values of a row: columns c0 .. c0 + 7 of the
+// tile (output o = row * N + n0 + c0), bias from shared memory (sb: the
+// tile's first column), ReLU, mask, BF16 or FP32 store.
+__device__ __forceinline__ void tm_store8(const uint32_t* r, int o, int c0, int nt, const float* sb,
+                                          const __nv_bfloat16* __restrict__ mask, void* __restrict__ out,
+                                          int out_f32, int relu, int vec_out) {
+    float v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        v[j] = __uint_as_float(r[j]);
+        if (sb && c0 + j < nt) v[j] += sb[c0 + j];
+        if (relu) v[j] = v[j] > 0.0f ? v[j] : 0.0f;
+    }
+    if (c0 + 8 <= nt && vec_out) {
+        if (mask) {
+            const uint4 mk = *reinterpret_cast<const uint4*>(mask + o);
+            const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (!(__bfloat162float(mb[j]) > 0.0f)) v[j] = 0.0f;
+        }
+        if (out_f32) {
+            float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
+            d[0] = make_float4(v[0], v[1], v[2], v[3]);
+            d[1] = make_float4(v[4], v[5], v[6], v[7]);
+        } else {
+            uint4 pk;
+            __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+            *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = pk;
+        }
+    } else {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            v[j] = __uint_as_float(r[j]);
-            if (bias && c0 + j < nt) v[j] += bias[n0 + c0 + j];
-            if (relu) v[j] = v[j] > 0.0f ? v[j] : 0.0f;
+            if (c0 + j >= nt) break;
+            float x = v[j];
+            if (mask && !(__bfloat162float(mask[o + j]) > 0.0f)) x = 0.0f;
+            if (out_f32) reinterpret_cast<float*>(out)[o + j] = x;
+            else reinterpret_cast<__nv_bfloat16*>(out)[o + j] = __float2bfloat16(x);
         }
-        if (c0 + 8 <= nt && vec_out) {
-            if (mask) {
-                const uint4 mk = *reinterpret_cast<const uint4*>(mask + o);
-                const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+    }
+}
+
+// Epilogue of one accumulator row (pixel `row`, outputs n0 .. n0 + nt - 1):
+// 32 columns per TMEM load and wait, then the rest 8 at a time.
+__device__ __forceinline__ void tm_store_row(uint32_t taddr, int row, int n0, int nt, int tile_n, int N,
+                                             const float* sb, const __nv_bfloat16* __restrict__ mask,
+                                             void* __restrict__ out, int out_f32, int relu, int vec_out) {
+    const int o = row * N + n0;
+    int c0 = 0;
+    for (; c0 + 32 <= tile_n; c0 += 32) {
+        uint32_t r[32];
+        tc_ld32_nowait(taddr + (uint32_t)c0, r);
+        tc_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 8; ++j)
-                    if (!(__bfloat162float(mb[j]) > 0.0f)) v[j] = 0.0f;
-            }
-            if (out_f32) {
-                float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(out) + o);
-                d[0] = make_float4(v[0], v[1], v[2], v[3]);
-                d[1] = make_float4(v[4], v[5], v[6], v[7]);
-            } else {
-                uint4 pk;
-                __nv_bfloat162* h2 = reinterpret_cast<__nv_bfloat162*>(&pk);
-#pragma unroll
-                for (int j = 0; j < 4; ++j) h2[j] = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
-                *reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(out) + o) = pk;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                if (c0 + j >= nt) break;
-                float x = v[j];
-                if (mask && !(__bfloat162float(mask[o + j]) > 0.0f)) x = 0.0f;
-                if (out_f32) reinterpret_cast<float*>(out)[o + j] = x;
-                else reinterpret_cast<__nv_bfloat16*>(out)[o + j] = __float2bfloat16(x);
-            }
-        }
+        for (int q = 0; q < 4; ++q)
+            if (c0 + 8 * q < nt) tm_store8(r + 8 * q, o + c0 + 8 * q, c0 + 8 * q, nt, sb, mask, out, out_f32, relu, vec_out);
+    }
+    for (; c0 < tile_n; c0 += 8) {
+        uint32_t r[8];
+        tc_ld8(taddr + (uint32_t)c0, r);
+        if (c0 < nt) tm_store8(r, o + c0, c0, nt, sb, mask, out, out_f32, relu, vec_out);
     }
 }
 
@@ -598,6 +632,7 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_conv_tma(const __grid_constan
     extern __shared__ unsigned char smem_raw[];
     unsigned char* const smem =
         smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);   // swizzled tiles start on 1024 B
+    __shared__ float s_bias[TM_BIAS_MAX];                               // the bias of all N outputs
     const int a_bytes = TC_M * kc * 2, b_bytes = tile_n * kc * 2;
     const int stage_bytes = a_bytes + b_bytes;                           // a multiple of 1024 (tile_n % 16 == 0)
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + stages * stage_bytes);
@@ -633,6 +668,9 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_conv_tma(const __grid_constan
         s_consumed = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    const bool sbias = bias && N <= TM_BIAS_MAX;
+    if (sbias)
+        for (int i = tid; i < N; i += TM_THREADS) s_bias[i] = bias[i];
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -712,7 +750,8 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_conv_tma(const __grid_constan
             const int m0 = (t / ntn) * TC_M, n0 = (t % ntn) * tile_n;
             const int row = m0 + warp * 32 + lane;
             tm_store_row(tmem + (uint32_t)(b * tmem_cols) + ((uint32_t)(warp * 32) << 16), row, n0,
-                         min(tile_n, N - n0), tile_n, N, bias, mask, out, out_f32, relu, vec_out);
+                         min(tile_n, N - n0), tile_n, N, sbias ? s_bias + n0 : (bias ? bias + n0 : nullptr), mask, out, out_f32, relu,
+                         vec_out);
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             mbar_arrive(smem_u32(&acc_empty[b]));
         }
@@ -738,11 +777,13 @@ __global__ void __launch_bounds__(TM_THREADS, 1) k_conv_tma(const __grid_constan
 // is 8 pixels (K) x 8 consecutive channels (16 bytes, M or N), exactly one
 // global 16-byte vector per row; core matrices are 128 B apart along M/N
 // (stride byte offset) and 128 * (rows / 8) B apart along K (leading byte
-// offset).  Requires cin % 8 == 0 and cout % 8 == 0.
+// offset).  Requires cin % 8 == 0 and cout % 8 == 0.  With db, the first
+// padding row of A (row M, present when M % 128 != 0) is all ones, so row M
+// of D is the bias gradient sum_p dY[p][co], added into db.
 __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __restrict__ X,
                                                          const __nv_bfloat16* __restrict__ dY, float* __restrict__ dw,
-                                                         ConvShape s, int M, int N, int npix, int kchunk, int tile_n,
-                                                         int tmem_cols) {
+                                                         float* __restrict__ db, ConvShape s, int M, int N, int npix,
+                                                         int kchunk, int tile_n, int tmem_cols) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int b_bytes = tile_n * TC_K * 2;
     unsigned char* const a_base = smem;
@@ -782,24 +823,48 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __
     // loaded one chunk ahead into registers
     constexpr int NA = TC_M / 8 / TC_PIX_STEP;
     uint4 va[NA];
+    // the row groups' taps and channels do not change along K: decode them once
+    int a_dy[NA], a_dx[NA], a_ci[NA], a_kind[NA];   // kind: 0 zero, 1 activation, 2 ones (bias row)
+#pragma unroll
+    for (int j = 0; j < NA; ++j) {
+        const int m = m0 + 8 * (g0 + TC_PIX_STEP * j);
+        const int tap = m < M ? m / s.cin : 0;
+        a_ci[j] = m - tap * s.cin;
+        a_dy[j] = tap_dy(tap, s.taps);
+        a_dx[j] = tap_dx(tap, s.taps);
+        a_kind[j] = m < M ? 1 : (db && m == M ? 2 : 0);
+    }
+    // this thread's pixel of chunk c, (image, row, column), advanced by TC_K per chunk
+    int c_pn = 0, c_py = 0, c_px = 0, c_at = -1;
     auto load_a = [&](int c) {
         const int p = kb + c * TC_K + kl;
-        int pn = 0, py = -1000000, px = 0;
-        if (p < ke) {
-            pn = p / hw;
-            const int rem = p - pn * hw;
-            py = rem / s.w;
-            px = rem - py * s.w;
+        if (c_at < 0) {
+            c_pn = p / hw;
+            const int rem = p - c_pn * hw;
+            c_py = rem / s.w;
+            c_px = rem - c_py * s.w;
+        } else {
+            c_px += TC_K * (c - c_at);
+            while (c_px >= s.w) {
+                c_px -= s.w;
+                if (++c_py == s.h) {
+                    c_py = 0;
+                    ++c_pn;
+                }
+            }
         }
+        c_at = c;
+        const bool live = p < ke;
 #pragma unroll
         for (int j = 0; j < NA; ++j) {
-            const int g = g0 + TC_PIX_STEP * j, m = m0 + 8 * g;
             va[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (m < M) {
-                const int tap = m / s.cin, ci = m - tap * s.cin;
-                const int yy = py + tap_dy(tap, s.taps), xx = px + tap_dx(tap, s.taps);
+            if (!live) continue;
+            if (a_kind[j] == 1) {
+                const int yy = c_py + a_dy[j], xx = c_px + a_dx[j];
                 if (yy >= 0 && yy < s.h && xx >= 0 && xx < s.w)
-                    va[j] = __ldg(reinterpret_cast<const uint4*>(X + ((pn * s.h + yy) * s.w + xx) * s.cin + ci));
+                    va[j] = __ldg(reinterpret_cast<const uint4*>(X + ((c_pn * s.h + yy) * s.w + xx) * s.cin + a_ci[j]));
+            } else if (a_kind[j] == 2) {
+                va[j] = make_uint4(0x3F80u, 0u, 0u, 0u);   // row M = ones (BF16 1.0): D[M][n] = bias gradient
             }
         }
     };
@@ -862,6 +927,12 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __
                 for (int j = 0; j < 8; ++j) {
                     if (c0 + j >= nt) break;
                     atomicAdd(dw + row * N + n0 + c0 + j, __uint_as_float(r[j]));
+                }
+            } else if (db && row == M) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (c0 + j >= nt) break;
+                    atomicAdd(db + n0 + c0 + j, __uint_as_float(r[j]));
                 }
             }
         }
@@ -947,13 +1018,16 @@ bool launch_tma(const void* A, const void* B, const float* bias, const void* mas
     const int tile_n = N <= 256 ? (int)((N + 15) & ~15LL) : 256;
     int cols = 32;
     while (cols < tile_n) cols <<= 1;
-    // 32-channel chunks (64-byte rows) when they waste fewer zero-filled channels
-    const int kc = (C < 128 && (C + 31) / 32 * 32 < (C + 63) / 64 * 64) ? 32 : 64;
+    // 32-channel chunks (64-byte rows) for narrow inputs; wider ones in 64-channel
+    // chunks: fewer copies and MMA steps per tile (a zero-filled tail is cheap)
+    const int kc = C <= 32 ? 32 : 64;
     const int cchunks = (C + kc - 1) / kc;
     // two CTAs per SM (two accumulator buffers each) while both fit in TMEM
     const int per_sm = 2 * cols <= 256 ? 2 : 1;
     const size_t stage_bytes = (size_t)TC_M * kc * 2 + (size_t)tile_n * kc * 2;
-    const size_t budget = (per_sm == 2 ? 110 : 220) * 1024 - 1024 - 128;
+    // dynamic shared memory per CTA: what is left of the SM's 228 KB after the
+    // static bias stage (TM_BIAS_MAX floats) and the per-CTA reservation
+    const size_t budget = (per_sm == 2 ? 104 : 214) * 1024 - 1024 - 128;
     const int stages = (int)std::min<size_t>(8, budget / stage_bytes);
     if (stages < 2) return false;
     CUtensorMap ma, mb;
@@ -1021,11 +1095,13 @@ bool launch_tc(const void* A, const void* B, const float* bias, const void* mask
 }
 
 // Launches the tcgen05 weight gradient; false when the shape is not one it takes.
-bool launch_wgrad_tc(const void* x, const void* dy, float* dw, ConvShape s, int splitk, cudaStream_t st, int* rc) {
+bool launch_wgrad_tc(const void* x, const void* dy, float* dw, float* db, ConvShape s, int splitk, cudaStream_t st,
+                     int* rc) {
     if (s.cin % 8 || s.cout % 8 || !aligned16(x) || !aligned16(dy)) return false;
     const long long npix = (long long)s.n * s.h * s.w;
     const long long cmax = s.cin > s.cout ? s.cin : s.cout;
     const long long M = (long long)s.taps * s.cin, N = s.cout;
+    if (db && M % TC_M == 0) return false;   // no free row for the bias
     if (npix * cmax * s.taps >= 2147483647LL || M * N >= 2147483647LL) return false;
     const int tile_n = N <= 256 ? (int)((N + 15) & ~15LL) : 256;
     int cols = 32;
@@ -1047,7 +1123,7 @@ bool launch_wgrad_tc(const void* x, const void* dy, float* dw, ConvShape s, int 
         return true;
     }
     const dim3 grid((unsigned)((M + TC_M - 1) / TC_M), (unsigned)((N + tile_n - 1) / tile_n), (unsigned)gz);
-    k_wgrad_tc<<<grid, TC_THREADS, smem, st>>>((const __nv_bfloat16*)x, (const __nv_bfloat16*)dy, dw, s, (int)M,
+    k_wgrad_tc<<<grid, TC_THREADS, smem, st>>>((const __nv_bfloat16*)x, (const __nv_bfloat16*)dy, dw, db, s, (int)M,
                                                (int)N, (int)npix, (int)kchunk, tile_n, cols);
     *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
     return true;
@@ -1355,21 +1431,26 @@ __global__ void __launch_bounds__(BG_THREADS) k_bias_grad8(const uint4* __restri
 
 // Weight gradient of a 1x1 convolution with few outputs (the network's head):
 // dw[ci][co] += sum_p x[p][ci] dy[p][co] for CIN inputs (a multiple of 8) and
-// COUT outputs; each thread accumulates all CIN * COUT products over a strided
-// set of pixels, then warp shuffles and one atomic per block and weight.
+// COUT outputs, and (db not NULL) db[co] += sum_p dy[p][co]; each thread
+// accumulates all products over a strided set of pixels, then warp shuffles
+// and one atomic per block and value.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(256) k_wgrad_small(const __nv_bfloat16* __restrict__ x,
                                                      const __nv_bfloat16* __restrict__ dy, float* __restrict__ dw,
-                                                     long long npix) {
-    __shared__ float red[8][CIN * COUT];
-    float acc[CIN * COUT];
+                                                     float* __restrict__ db, long long npix) {
+    constexpr int NA = CIN * COUT + COUT;       // weights, then the bias (sum of dy)
+    __shared__ float red[8][NA];
+    float acc[NA];
 #pragma unroll
-    for (int k = 0; k < CIN * COUT; ++k) acc[k] = 0.0f;
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0f;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npix;
          p += (long long)blockDim.x * gridDim.x) {
         float d[COUT];
 #pragma unroll
-        for (int o = 0; o < COUT; ++o) d[o] = __bfloat162float(dy[p * COUT + o]);
+        for (int o = 0; o < COUT; ++o) {
+            d[o] = __bfloat162float(dy[p * COUT + o]);
+            acc[CIN * COUT + o] += d[o];
+        }
         const uint4* xr = reinterpret_cast<const uint4*>(x + p * CIN);
 #pragma unroll
         for (int v = 0; v < CIN / 8; ++v) {
@@ -1383,30 +1464,86 @@ __global__ void __launch_bounds__(256) k_wgrad_small(const __nv_bfloat16* __rest
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < CIN * COUT; ++k) {
+    for (int k = 0; k < NA; ++k) {
         float v = acc[k];
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
         if (lane == 0) red[warp][k] = v;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < CIN * COUT; k += blockDim.x) {
+    for (int k = threadIdx.x; k < NA; k += blockDim.x) {
         float v = 0.0f;
         for (int wi = 0; wi < 8; ++wi) v += red[wi][k];
-        atomicAdd(dw + k, v);
+        if (k < CIN * COUT) atomicAdd(dw + k, v);
+        else if (db) atomicAdd(db + (k - CIN * COUT), v);
     }
 }
 
+// Input gradient of a 1x1 convolution with few outputs (the network's head):
+// dx[p][ci] = sum_co dy[p][co] w[ci][co], zeroed where mask[p][ci] <= 0 (mask
+// may be NULL); one pixel per thread, the CIN x COUT weights in shared memory.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_dgrad_small(const __nv_bfloat16* __restrict__ dy,
+                                                     const __nv_bfloat16* __restrict__ w,
+                                                     const __nv_bfloat16* __restrict__ mask,
+                                                     __nv_bfloat16* __restrict__ dx, long long npix) {
+    __shared__ float sw[CIN * COUT];
+    for (int k = threadIdx.x; k < CIN * COUT; k += blockDim.x) sw[k] = __bfloat162float(w[k]);
+    __syncthreads();
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= npix) return;
+    float d[COUT];
+#pragma unroll
+    for (int o = 0; o < COUT; ++o) d[o] = __bfloat162float(dy[p * COUT + o]);
+#pragma unroll
+    for (int v = 0; v < CIN / 8; ++v) {
+        float r[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            float a = 0.0f;
+#pragma unroll
+            for (int o = 0; o < COUT; ++o) a = fmaf(d[o], sw[(8 * v + j) * COUT + o], a);
+            r[j] = a;
+        }
+        if (mask) {
+            float m[8];
+            unpack8(reinterpret_cast<const uint4*>(mask + p * CIN)[v], m);
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                if (!(m[j] > 0.0f)) r[j] = 0.0f;
+        }
+        reinterpret_cast<uint4*>(dx + p * CIN)[v] = pack8(r);
+    }
+}
+
+// Launches k_dgrad_small for the shapes it is instantiated for; false otherwise.
+bool launch_dgrad_small(const void* dy, const void* w, const void* mask, void* dx, ConvShape s, cudaStream_t st,
+                        int* rc) {
+    if (s.taps != 1 || !aligned16(dx) || (mask && !aligned16(mask))) return false;
+    const long long npix = (long long)s.n * s.h * s.w;
+    const unsigned grid = (unsigned)((npix + 255) / 256);
+    const __nv_bfloat16 *dyb = (const __nv_bfloat16*)dy, *wb = (const __nv_bfloat16*)w,
+                        *mb = (const __nv_bfloat16*)mask;
+    __nv_bfloat16* dxb = (__nv_bfloat16*)dx;
+    if (s.cout == 4 && s.cin == 8) k_dgrad_small<8, 4><<<grid, 256, 0, st>>>(dyb, wb, mb, dxb, npix);
+    else if (s.cout == 4 && s.cin == 16) k_dgrad_small<16, 4><<<grid, 256, 0, st>>>(dyb, wb, mb, dxb, npix);
+    else if (s.cout == 4 && s.cin == 24) k_dgrad_small<24, 4><<<grid, 256, 0, st>>>(dyb, wb, mb, dxb, npix);
+    else if (s.cout == 4 && s.cin == 32) k_dgrad_small<32, 4><<<grid, 256, 0, st>>>(dyb, wb, mb, dxb, npix);
+    else return false;
+    *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+    return true;
+}
+
 // Launches k_wgrad_small for the shapes it is instantiated for; false otherwise.
-bool launch_wgrad_small(const void* x, const void* dy, float* dw, ConvShape s, cudaStream_t st, int* rc) {
+bool launch_wgrad_small(const void* x, const void* dy, float* dw, float* db, ConvShape s, cudaStream_t st, int* rc) {
     if (s.taps != 1 || !aligned16(x)) return false;
     const long long npix = (long long)s.n * s.h * s.w;
     const unsigned grid = (unsigned)std::min<long long>(4 * 152, (npix + 255) / 256);
-    const __nv_bfloat16 *xb = (const __nv_bfloat16*)x, *db = (const __nv_bfloat16*)dy;
-    if (s.cout == 4 && s.cin == 8) k_wgrad_small<8, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
-    else if (s.cout == 4 && s.cin == 16) k_wgrad_small<16, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
-    else if (s.cout == 4 && s.cin == 24) k_wgrad_small<24, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
-    else if (s.cout == 4 && s.cin == 32) k_wgrad_small<32, 4><<<grid, 256, 0, st>>>(xb, db, dw, npix);
+    const __nv_bfloat16 *xb = (const __nv_bfloat16*)x, *dyb = (const __nv_bfloat16*)dy;
+    if (s.cout == 4 && s.cin == 8) k_wgrad_small<8, 4><<<grid, 256, 0, st>>>(xb, dyb, dw, db, npix);
+    else if (s.cout == 4 && s.cin == 16) k_wgrad_small<16, 4><<<grid, 256, 0, st>>>(xb, dyb, dw, db, npix);
+    else if (s.cout == 4 && s.cin == 24) k_wgrad_small<24, 4><<<grid, 256, 0, st>>>(xb, dyb, dw, db, npix);
+    else if (s.cout == 4 && s.cin == 32) k_wgrad_small<32, 4><<<grid, 256, 0, st>>>(xb, dyb, dw, db, npix);
     else return false;
     *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
     return true;
@@ -1439,18 +1576,30 @@ extern "C" int clb_nop_conv_dgrad(const void* dy, const void* w, const void* mas
     int rc;
     if (launch_tma<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, (cudaStream_t)stream, &rc)) return rc;
     if (launch_tc<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, K, (cudaStream_t)stream, &rc)) return rc;
+    if (launch_dgrad_small(dy, w, mask, dx, s, (cudaStream_t)stream, &rc)) return rc;
     return launch_gemm<DGRAD>(dy, w, nullptr, mask, dx, 0, 0, s, M, cin, K, 1, (cudaStream_t)stream);
+}
+
+extern "C" int clb_nop_conv_wgrad_bias(const void* x, const void* dy, float* dw, float* db, int32_t n, int32_t h,
+                                       int32_t wd, int32_t cin, int32_t cout, int32_t taps, int32_t splitk,
+                                       void* stream) {
+    if (!x || !dy || !dw || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
+    const ConvShape s{n, h, wd, cin, cout, taps};
+    const cudaStream_t st = (cudaStream_t)stream;
+    int rc;
+    if (launch_wgrad_tc(x, dy, dw, db, s, splitk, st, &rc) || launch_wgrad_small(x, dy, dw, db, s, st, &rc)) return rc;
+    if (db) {   // the generic paths: bias gradient in its own pass
+        rc = clb_nop_bias_grad(dy, db, (int64_t)n * h * wd, cout, stream);
+        if (rc != CLB_NOP_OK) return rc;
+        if (launch_wgrad_tc(x, dy, dw, nullptr, s, splitk, st, &rc)) return rc;
+    }
+    return launch_gemm<WGRAD>(x, dy, nullptr, nullptr, dw, 1, 0, s, (long long)taps * cin, cout, (long long)n * h * wd,
+                              splitk, st);
 }
 
 extern "C" int clb_nop_conv_wgrad(const void* x, const void* dy, float* dw, int32_t n, int32_t h, int32_t wd,
                                   int32_t cin, int32_t cout, int32_t taps, int32_t splitk, void* stream) {
-    if (!x || !dy || !dw || bad_shape(n, h, wd, cin, cout, taps)) return CLB_NOP_ERR_ARG;
-    const ConvShape s{n, h, wd, cin, cout, taps};
-    int rc;
-    if (launch_wgrad_tc(x, dy, dw, s, splitk, (cudaStream_t)stream, &rc)) return rc;
-    if (launch_wgrad_small(x, dy, dw, s, (cudaStream_t)stream, &rc)) return rc;
-    return launch_gemm<WGRAD>(x, dy, nullptr, nullptr, dw, 1, 0, s, (long long)taps * cin, cout, (long long)n * h * wd,
-                              splitk, (cudaStream_t)stream);
+    return clb_nop_conv_wgrad_bias(x, dy, dw, nullptr, n, h, wd, cin, cout, taps, splitk, stream);
 }
 
 extern "C" int clb_nop_bias_grad(const void* dy, float* db, int64_t npix, int32_t c, void* stream) {
@@ -1524,18 +1673,83 @@ extern "C" int clb_nop_mse(const float* pred, const float* target, const float* 
     return status();
 }
 
-extern "C" int clb_nop_adam(float* w, const float* g, float* m, float* v, void* wb, int64_t n, float lr, float b1,
-                            float b2, float eps, int32_t t, void* stream) {
-    if (!w || !g || !m || !v || n < 1 || t < 1) return CLB_NOP_ERR_ARG;
-    float c1 = 1.0f, c2 = 1.0f, p1 = 1.0f, p2 = 1.0f;
+namespace {
+// Bias corrections 1 - b1^t, 1 - b2^t (the power by repeated products, as
+// the FP32 moments see it).
+void adam_corrections(float b1, float b2, int32_t t, float& c1, float& c2) {
+    float p1 = 1.0f, p2 = 1.0f;
     for (int i = 0; i < t && i < 100000; ++i) {
         p1 *= b1;
         p2 *= b2;
     }
     c1 = 1.0f - p1;
     c2 = 1.0f - p2;
+}
+
+constexpr int ADAM_SEGS = 32;
+struct AdamSegs {
+    clb_nop_adam_seg s[ADAM_SEGS];
+    int first[ADAM_SEGS + 1];   // first block of each segment
+    int n;
+};
+
+__global__ void k_adam_multi(const AdamSegs S, float lr, float b1, float b2, float eps, float c1, float c2) {
+    int k = 0;
+    while (k + 1 < S.n && (int)blockIdx.x >= S.first[k + 1]) ++k;
+    const clb_nop_adam_seg& q = S.s[k];
+    const long long i = (long long)(blockIdx.x - S.first[k]) * blockDim.x + threadIdx.x;
+    if (i >= q.n) return;
+    const float gi = q.g[i];
+    const float mi = b1 * q.m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * q.v[i] + (1.0f - b2) * gi * gi;
+    q.m[i] = mi;
+    q.v[i] = vi;
+    const float wi = q.w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    q.w[i] = wi;
+    const __nv_bfloat16 wh = __float2bfloat16(wi);
+    if (q.wb) reinterpret_cast<__nv_bfloat16*>(q.wb)[i] = wh;
+    if (q.wbt) {
+        const int r = (int)(i / q.cols), c = (int)(i - (long long)r * q.cols);
+        reinterpret_cast<__nv_bfloat16*>(q.wbt)[(long long)c * q.rows + r] = wh;
+    }
+}
+}  // namespace
+
+extern "C" int clb_nop_adam(float* w, const float* g, float* m, float* v, void* wb, int64_t n, float lr, float b1,
+                            float b2, float eps, int32_t t, void* stream) {
+    if (!w || !g || !m || !v || n < 1 || t < 1) return CLB_NOP_ERR_ARG;
+    float c1, c2;
+    adam_corrections(b1, b2, t, c1, c2);
     k_adam<<<nblk(n), 256, 0, (cudaStream_t)stream>>>(w, g, m, v, (__nv_bfloat16*)wb, n, lr, b1, b2, eps, c1, c2);
     return status();
+}
+
+extern "C" int clb_nop_adam_multi(const clb_nop_adam_seg* segs, int32_t nseg, float lr, float b1, float b2, float eps,
+                                  int32_t t, void* stream) {
+    if (!segs || nseg < 1 || t < 1) return CLB_NOP_ERR_ARG;
+    for (int k = 0; k < nseg; ++k) {
+        const clb_nop_adam_seg& q = segs[k];
+        if (!q.w || !q.g || !q.m || !q.v || q.n < 1 || (q.wbt && (q.rows < 1 || q.cols < 1 ||
+                                                                   (int64_t)q.rows * q.cols != q.n)))
+            return CLB_NOP_ERR_ARG;
+    }
+    float c1, c2;
+    adam_corrections(b1, b2, t, c1, c2);
+    for (int k0 = 0; k0 < nseg; k0 += ADAM_SEGS) {
+        AdamSegs S;
+        S.n = std::min(ADAM_SEGS, nseg - k0);
+        long long blocks = 0;
+        for (int k = 0; k < S.n; ++k) {
+            S.s[k] = segs[k0 + k];
+            S.first[k] = (int)blocks;
+            blocks += (S.s[k].n + 255) / 256;
+        }
+        if (blocks >= 2147483647LL) return CLB_NOP_ERR_ARG;
+        S.first[S.n] = (int)blocks;
+        k_adam_multi<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(S, lr, b1, b2, eps, c1, c2);
+        if (cudaGetLastError() != cudaSuccess) return CLB_NOP_ERR_CUDA;
+    }
+    return CLB_NOP_OK;
 }
 
 extern "C" int clb_nop_cast_bf16(const float* x, void* y, int64_t n, void* stream) {

@@ -37,6 +37,12 @@ N_IN, N_OUT = 8, 4
 _VP = ctypes.c_void_p
 
 
+class AdamSeg(ctypes.Structure):
+    """clb_nop_adam_seg of include/clb_nop.h."""
+    _fields_ = [("w", _VP), ("g", _VP), ("m", _VP), ("v", _VP), ("wb", _VP), ("wbt", _VP), ("n", ctypes.c_int64),
+                ("rows", ctypes.c_int32), ("cols", ctypes.c_int32)]
+
+
 def _lib():
     L = clb.load()
     if not getattr(L, "_nop_ready", False):
@@ -44,12 +50,14 @@ def _lib():
         L.clb_nop_conv_fwd.argtypes = [_VP, _VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_conv_dgrad.argtypes = [_VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_conv_wgrad.argtypes = [_VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, _VP]
+        L.clb_nop_conv_wgrad_bias.argtypes = [_VP, _VP, _VP, _VP, i32, i32, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_bias_grad.argtypes = [_VP, _VP, i64, i32, _VP]
         L.clb_nop_pool2.argtypes = [_VP, _VP, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_up2.argtypes = [_VP, _VP, i32, i32, i32, i32, i32, _VP]
         L.clb_nop_concat.argtypes = [_VP, _VP, _VP, i64, i32, i32, i32, _VP]
         L.clb_nop_mse.argtypes = [_VP, _VP, _VP, i32, _VP, _VP, i64, _VP]
         L.clb_nop_adam.argtypes = [_VP, _VP, _VP, _VP, _VP, i64, f32, f32, f32, f32, i32, _VP]
+        L.clb_nop_adam_multi.argtypes = [ctypes.POINTER(AdamSeg), i32, f32, f32, f32, f32, i32, _VP]
         L.clb_nop_cast_bf16.argtypes = [_VP, _VP, i64, _VP]
         L.clb_nop_zero.argtypes = [_VP, i64, _VP]
         L.clb_nop_transpose.argtypes = [_VP, _VP, i32, i32, _VP]
@@ -197,7 +205,29 @@ class Net:
                 (c4 + c3, c3), (c3, c3), (c3 + c2, c2), (c2, c2), (c2 + c1, c1), (c1, c1)]
         layers = [Conv(torch, a, b, 9, True, rng) for a, b in spec]
         layers.append(Conv(torch, c1, cout, 1, False, rng))
-        return cls(layers, torch)
+        net = cls(layers, torch)
+        net._flat_grads()
+        return net
+
+    def _flat_grads(self):
+        """All weight and bias gradients as views of one buffer (cleared by
+        one call per backward pass), and the Adam segment table."""
+        t = self.torch
+        total = sum(l.gw.numel() + l.gb.numel() for l in self.layers)
+        self.grads = t.zeros(total, dtype=t.float32, device="cuda")
+        off = 0
+        for l in self.layers:
+            n = l.gw.numel()
+            l.gw = self.grads[off:off + n].view(l.w.shape)
+            off += n
+            l.gb = self.grads[off:off + l.b.numel()]
+            off += l.b.numel()
+        segs = []
+        for l in self.layers:
+            segs.append(AdamSeg(_p(l.w), _p(l.gw), _p(l.mw), _p(l.vw), _p(l.wb), _p(l.wbt), l.w.numel(),
+                                l.taps * l.cin, l.cout))
+            segs.append(AdamSeg(_p(l.b), _p(l.gb), _p(l.mb), _p(l.vb), None, None, l.b.numel(), 1, l.b.numel()))
+        self._segs = (AdamSeg * len(segs))(*segs)
 
     @property
     def nparams(self):
@@ -275,8 +305,8 @@ class Net:
         """Accumulate l's weight and bias gradients; return dx (BF16) masked
         by `mask` > 0 (the ReLU of the layer that produced x) if given."""
         lib, t = _lib(), self.torch
-        _ok(lib.clb_nop_conv_wgrad(_p(x), _p(dy), _p(l.gw), n, h, w, l.cin, l.cout, l.taps, 0, None), "wgrad")
-        _ok(lib.clb_nop_bias_grad(_p(dy), _p(l.gb), n * h * w, l.cout, None), "bias_grad")
+        _ok(lib.clb_nop_conv_wgrad_bias(_p(x), _p(dy), _p(l.gw), _p(l.gb), n, h, w, l.cin, l.cout, l.taps, 0, None),
+            "wgrad")
         if not want_dx:
             return None
         dx = t.empty((n, h, w, l.cin), dtype=t.bfloat16, device="cuda")
@@ -299,9 +329,7 @@ class Net:
     def backward(self, dout, A, n, h, w):
         L, t, lib = self.layers, self.torch, _lib()
         c1, c2, c3, c4 = L[0].cout, L[2].cout, L[4].cout, L[6].cout
-        for l in L:
-            _ok(lib.clb_nop_zero(_p(l.gw), l.gw.numel() * 4, None), "zero")
-            _ok(lib.clb_nop_zero(_p(l.gb), l.gb.numel() * 4, None), "zero")
+        _ok(lib.clb_nop_zero(_p(self.grads), self.grads.numel() * 4, None), "zero")
         h2, w2, h4, w4, h8, w8 = h // 2, w // 2, h // 4, w // 4, h // 8, w // 8
         d = self._grads(L[14], A[14], dout, n, h, w, A[14])
         d = self._grads(L[13], A[13], d, n, h, w, A[13])
@@ -335,13 +363,8 @@ class Net:
         self._grads(L[0], A["x"], d, n, h, w, None, want_dx=False)
 
     def adam(self, step, lr, b1=0.9, b2=0.999, eps=1e-8):
-        lib = _lib()
-        for l in self.layers:
-            _ok(lib.clb_nop_adam(_p(l.w), _p(l.gw), _p(l.mw), _p(l.vw), _p(l.wb), l.w.numel(), lr, b1, b2, eps, step,
-                                 None), "adam")
-            _ok(lib.clb_nop_adam(_p(l.b), _p(l.gb), _p(l.mb), _p(l.vb), None, l.b.numel(), lr, b1, b2, eps, step,
-                                 None), "adam")
-            l.refresh_t()
+        # one launch: every layer's weights (BF16 copy and its transpose refreshed) and biases
+        _ok(_lib().clb_nop_adam_multi(self._segs, len(self._segs), lr, b1, b2, eps, step, None), "adam")
 
     def loss_and_grad(self, out, target, weights=None):
         """Channel-weighted MSE and its gradient (weights: device FP32, one per

@@ -92,7 +92,12 @@ def test_conv_forward(lib, shape, relu):
         _close(y16.cpu(), ref, 8e-3)
 
 
-@pytest.mark.parametrize("shape", SHAPES + [PRODUCTION])
+# the network's head (1x1, 24 -> 4): weight and input gradients on CUDA-core
+# kernels, small and at the training batch
+HEADS = [(2, 8, 12, 24, 4, 1), (3, 5, 7, 8, 4, 1), (16, 128, 128, 24, 4, 1)]
+
+
+@pytest.mark.parametrize("shape", SHAPES + [PRODUCTION] + HEADS)
 def test_conv_input_gradient(lib, shape):
     n, h, w, cin, cout, taps = shape
     x = _bf((n, h, w, cin), 4)
@@ -106,9 +111,6 @@ def test_conv_input_gradient(lib, shape):
     assert lib.clb_nop_check(None) == 0
     _close(dx.cpu(), ref, 8e-3)
 
-
-# the network's head (1x1, 24 -> 4) on its own CUDA-core kernel, small and at the training batch
-HEADS = [(2, 8, 12, 24, 4, 1), (3, 5, 7, 8, 4, 1), (16, 128, 128, 24, 4, 1)]
 
 
 @pytest.mark.parametrize("shape,splitk", [(s, k) for s in SHAPES for k in (1, 7)] + [(PRODUCTION, 0)] +
@@ -124,6 +126,12 @@ def test_conv_weight_gradient(lib, shape, splitk):
     dw = torch.zeros((taps * cin, cout), device="cuda")
     assert lib.clb_nop_conv_wgrad(_p(x.cuda()), _p(dy.cuda()), _p(dw), n, h, w, cin, cout, taps, splitk, None) == 0
     _close(dw.cpu(), wr.grad, 1e-5)
+    # the same pass with the bias gradient (a row of ones on the tensor-core path)
+    dw2, db = torch.zeros_like(dw), torch.zeros(cout, device="cuda")
+    assert lib.clb_nop_conv_wgrad_bias(_p(x.cuda()), _p(dy.cuda()), _p(dw2), _p(db), n, h, w, cin, cout, taps, splitk,
+                                       None) == 0
+    _close(dw2.cpu(), wr.grad, 1e-5)
+    _close(db.cpu(), dy.double().sum(dim=(0, 1, 2)).float(), 1e-5)
 
 
 def test_transpose(lib):
@@ -223,6 +231,32 @@ def test_mse_and_adam(lib):
         assert lib.clb_nop_adam(_p(wd), _p(gd), _p(m), _p(v), _p(wb), n, 1e-2, 0.9, 0.999, 1e-8, t, None) == 0
     _close(wd.cpu(), wr.detach(), 1e-6)
     assert torch.equal(wb.cpu(), wd.cpu().to(torch.bfloat16))
+
+
+def test_adam_multi_matches_the_single_tensor_step(lib):
+    """Several tensors (more than one launch's 32) in one call: the same values
+    as clb_nop_adam one tensor at a time, and the transposed BF16 copy."""
+    from paper_2110_05943_gb300 import surrogate
+    g = torch.Generator().manual_seed(23)
+    shapes = [(216, 24), (1, 24), (72, 5), (1, 1)] * 9                     # 36 segments
+    ts = []
+    for r, c in shapes:
+        w, gr = torch.randn((r, c), generator=g).cuda(), torch.randn((r, c), generator=g).cuda()
+        ts.append(dict(r=r, c=c, w=w, g=gr, m=torch.zeros_like(w), v=torch.zeros_like(w),
+                       wb=torch.empty((r, c), device="cuda", dtype=torch.bfloat16),
+                       wbt=torch.empty((c, r), device="cuda", dtype=torch.bfloat16),
+                       w1=w.clone(), m1=torch.zeros_like(w), v1=torch.zeros_like(w)))
+    segs = (surrogate.AdamSeg * len(ts))(*[surrogate.AdamSeg(_p(q["w"]), _p(q["g"]), _p(q["m"]), _p(q["v"]), _p(q["wb"]),
+                                                             _p(q["wbt"]), q["r"] * q["c"], q["r"], q["c"]) for q in ts])
+    for t in range(1, 4):
+        assert lib.clb_nop_adam_multi(segs, len(ts), 1e-2, 0.9, 0.999, 1e-8, t, None) == 0
+        for q in ts:
+            assert lib.clb_nop_adam(_p(q["w1"]), _p(q["g"]), _p(q["m1"]), _p(q["v1"]), None, q["r"] * q["c"], 1e-2, 0.9,
+                                    0.999, 1e-8, t, None) == 0
+    for q in ts:
+        assert torch.equal(q["w"], q["w1"]) and torch.equal(q["m"], q["m1"]) and torch.equal(q["v"], q["v1"])
+        assert torch.equal(q["wb"], q["w"].to(torch.bfloat16))
+        assert torch.equal(q["wbt"], q["wb"].t())
 
 
 class _RefNet(torch.nn.Module):
