@@ -945,6 +945,168 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(const __nv_bfloat16* __
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
 }
 
+// ---------------------------------------------------------------- TMA weight gradient
+// Weight gradient fed by the Tensor Memory Accelerator: D[m][n] = sum over
+// pixels p of A[m][p] B[n][p] with both operands MN-major (channels
+// contiguous, pixels along K), read straight from the NHWC tensors.  The M
+// rows of a tile are "atoms" of AW channels (AW = 32 with the 64-byte
+// swizzle, or 64 with the 128-byte one): atom a = (tap a / apt, channels
+// (a % apt) AW ...), loaded per 64-pixel K chunk as one 4-D box of X shifted
+// by the tap (zero fill at the image borders and past the last channel).
+// B atoms are BW-channel boxes of dY.  The canonical MN-major swizzled
+// layout: an atom's 64 K rows of 2 AW bytes in 8-row groups (stride byte
+// offset 16 AW), atoms one box apart (leading byte offset).  Slots past the
+// last atom hold zeros; with db the first of them is a row of ones, whose D
+// row is the bias gradient sum_p dY[p][n].  Those slots are written once per
+// stage before the loop and never loaded.  Roles and bounded waits as in
+// k_conv_tma's first form: thread 0 issues the copies into a ring of
+// `stages` buffers, thread 32 the four K = 16 MMAs per chunk; the four warps
+// add their rows to dw (FP32 atomics: the pixel sum is split over gridDim.z).
+constexpr int WG_K = 64;   // pixels per K chunk
+
+__device__ __forceinline__ uint64_t tc_desc_mn(uint32_t addr, uint32_t lbo, int row_bytes) {
+    const uint64_t mode = row_bytes == 128 ? 2ull : 4ull;
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((8 * row_bytes) >> 4) << 32) | (1ull << 46) | (mode << 61);
+}
+
+__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tma(const __grid_constant__ CUtensorMap mapA,
+                                                          const __grid_constant__ CUtensorMap mapB,
+                                                          float* __restrict__ dw, float* __restrict__ db, ConvShape s,
+                                                          int aw, int apt, int bw, int tile_n, int tmem_cols,
+                                                          int stages, int chunks_per_cta, int nchunks, int ones_atom) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* const smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+    const int a_atoms = TC_M / aw, atom_b = WG_K * aw * 2, a_bytes = a_atoms * atom_b;
+    const int b_atoms = tile_n / bw, batom_b = WG_K * bw * 2;
+    const int stage_bytes = a_bytes + b_atoms * batom_b;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + stages * stage_bytes);
+    uint64_t* empty = full + stages;
+    uint64_t* done = empty + stages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int s_issued, s_consumed;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int atom0 = blockIdx.x * a_atoms, n0 = blockIdx.y * tile_n;
+    const int atoms = s.taps * apt;
+    const int na_real = max(0, min(a_atoms, atoms - atom0));
+    const int c_begin = blockIdx.z * chunks_per_cta, c_end = min(nchunks, c_begin + chunks_per_cta);
+    const int hw = s.h * s.w;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < stages; ++i) {
+            mbar_init(smem_u32(&full[i]));
+            mbar_init(smem_u32(&empty[i]));
+        }
+        mbar_init(smem_u32(done));
+        s_issued = 0;
+        s_consumed = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // slots past the last atom: zeros, and the row of ones (element (k, 0) of
+    // the atom for every K row k, at its swizzled place: the 16-byte chunk
+    // index of row k is XORed with k / 2 mod 4 (64-byte rows) or k mod 8 (128-byte))
+    for (int st = 0; st < stages; ++st)
+        for (int j = na_real; j < a_atoms; ++j) {
+            unsigned char* at = smem + st * stage_bytes + j * atom_b;
+            for (int i = tid; i < atom_b / 16; i += TC_THREADS) reinterpret_cast<uint4*>(at)[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    __syncthreads();
+    if (ones_atom >= atom0 + na_real && ones_atom < atom0 + a_atoms && tid < WG_K)
+        for (int st = 0; st < stages; ++st) {
+            const int k = tid, rb = 2 * aw;
+            const int chunk = rb == 128 ? (k & 7) : ((k >> 1) & 3);
+            unsigned char* at = smem + st * stage_bytes + (ones_atom - atom0) * atom_b;
+            *reinterpret_cast<__nv_bfloat16*>(at + k * rb + 16 * chunk) = __float2bfloat16(1.0f);
+        }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    bool ok = true;
+    const int niter = c_end - c_begin;
+    if (tid == 0) {   // producer
+        int it = 0;
+        for (; it < niter; ++it) {
+            const int st = it % stages;
+            if (it >= stages && !mbar_wait_try(smem_u32(&empty[st]), ((it / stages) - 1) & 1, TC_TIMEOUT_CYCLES)) {
+                ok = false;
+                break;
+            }
+            const int p0 = (c_begin + it) * WG_K, img = p0 / hw, rem = p0 - img * hw;
+            const int h0 = rem / s.w, w0 = rem - h0 * s.w;
+            const uint32_t fb = smem_u32(&full[st]), base = smem_u32(smem + st * stage_bytes);
+            mbar_expect_tx(fb, (uint32_t)(na_real * atom_b + b_atoms * batom_b));
+            for (int j = 0; j < na_real; ++j) {
+                const int a = atom0 + j, tap = a / apt, c0 = (a - tap * apt) * aw;
+                tma_load_4d(base + j * atom_b, &mapA, fb, c0, w0 + tap_dx(tap, s.taps), h0 + tap_dy(tap, s.taps), img);
+            }
+            for (int j = 0; j < b_atoms; ++j) tma_load_4d(base + a_bytes + j * batom_b, &mapB, fb, n0 + j * bw, w0, h0, img);
+        }
+        s_issued = it;
+    } else if (tid == 32) {   // MMA issuer
+        const uint32_t idesc = tc_idesc(tile_n) | (1u << 15) | (1u << 16);   // A and B MN-major
+        int it = 0;
+        for (; it < niter; ++it) {
+            const int st = it % stages;
+            if (!mbar_wait_try(smem_u32(&full[st]), (it / stages) & 1, TC_TIMEOUT_CYCLES)) {
+                ok = false;
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(smem + st * stage_bytes), b0 = a0 + a_bytes;
+#pragma unroll
+            for (int ks = 0; ks < WG_K / 16; ++ks)   // 16 K rows = two 8-row groups
+                tc_mma(tmem, tc_desc_mn(a0 + ks * 32 * aw, atom_b, 2 * aw), tc_desc_mn(b0 + ks * 32 * bw, batom_b, 2 * bw),
+                       idesc, (it > 0 || ks > 0) ? 1u : 0u);
+            tc_commit(smem_u32(&empty[st]));
+        }
+        s_consumed = it;
+        tc_commit(smem_u32(done));
+    }
+    ok = ok && mbar_wait_try(smem_u32(done), 0u, TC_TIMEOUT_CYCLES);
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) {
+        for (int it = s_consumed; it < s_issued; ++it)
+            mbar_wait_try(smem_u32(&full[it % stages]), (it / stages) & 1, TC_TIMEOUT_CYCLES);
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && niter > 0) {
+        const int r = warp * 32 + lane, atom = atom0 + r / aw, within = r - (r / aw) * aw;
+        float* dst = nullptr;
+        if (atom < atoms) {
+            const int tap = atom / apt, ci = (atom - tap * apt) * aw + within;
+            if (ci < s.cin) dst = dw + (size_t)(tap * s.cin + ci) * s.cout + n0;
+        } else if (db && atom == ones_atom && within == 0) {
+            dst = db + n0;
+        }
+        const int nt = min(tile_n, s.cout - n0);
+        for (int c0 = 0; c0 < tile_n; c0 += 32) {
+            uint32_t v[32];
+            tc_ld32_nowait(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tc_wait_ld();
+            if (dst)
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (c0 + j < nt) atomicAdd(dst + c0 + j, __uint_as_float(v[j]));
+        }
+    } else if (!ok && tid == 0) {
+        atomicExch(&g_nop_timeout, 1u);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 // Streaming multiprocessors of the current device (looked up once).
@@ -1091,6 +1253,78 @@ bool launch_tc(const void* A, const void* B, const float* bias, const void* mask
                                                     (const __nv_bfloat16*)mask, out, out_f32, relu, s, (int)M, (int)N,
                                                     (int)K, tile_n, cols, vec_out);
     *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+    return true;
+}
+
+// Launches the TMA-fed weight gradient; false when the shape is not one it
+// takes (chunks of 64 pixels inside one image: width a multiple of 64, or a
+// divisor of 64 with the height a multiple of 64 / width; channel counts
+// multiples of 8, at most 256 outputs per tile).  *bias_done tells whether
+// db was filled through the row of ones (no free atom slot: not).
+bool launch_wgrad_tma(const void* x, const void* dy, float* dw, float* db, ConvShape s, int splitk, cudaStream_t st,
+                      int* rc, bool* bias_done) {
+    *bias_done = false;
+    if (s.cin % 8 || s.cout % 8 || !aligned16(x) || !aligned16(dy)) return false;
+    if (s.taps != 9 && s.taps != 1) return false;
+    int wbox, hbox;
+    if (s.w >= WG_K) {
+        if (s.w % WG_K) return false;
+        wbox = WG_K;
+        hbox = 1;
+    } else {
+        if (WG_K % s.w || s.h % (WG_K / s.w)) return false;
+        wbox = s.w;
+        hbox = WG_K / s.w;
+    }
+    const long long npix = (long long)s.n * s.h * s.w;
+    if (npix * (s.cin > s.cout ? s.cin : s.cout) * s.taps >= 2147483647LL) return false;
+    const int aw = s.cin <= 32 ? 32 : 64, apt = (s.cin + aw - 1) / aw, atoms = s.taps * apt;
+    const int a_atoms = TC_M / aw;
+    const int bw = s.cout <= 32 ? 32 : 64, batoms_all = (s.cout + bw - 1) / bw;
+    const int b_atoms = std::min(batoms_all, 256 / bw), tile_n = b_atoms * bw;
+    const int ntn = (batoms_all + b_atoms - 1) / b_atoms;
+    const int ones_atom = (db && atoms % a_atoms) ? atoms : -1;
+    const int mtiles = (atoms + a_atoms - 1) / a_atoms;
+    int cols = 32;
+    while (cols < tile_n) cols <<= 1;
+    const size_t stage_bytes = (size_t)TC_M * 2 * WG_K + (size_t)tile_n * 2 * WG_K;
+    const int stages = (int)std::min<size_t>(6, std::max<size_t>(2, (100 * 1024) / stage_bytes));
+    const size_t smem = 1024 + stages * stage_bytes + (2 * stages + 1) * 8 + 16;
+    const int nchunks = (int)(npix / WG_K);
+    const long long tiles = (long long)mtiles * ntn;
+    if (splitk < 1) {
+        // automatic: about three CTAs per SM, each with at least 4 chunks
+        const long long want = (3LL * sm_count() + tiles - 1) / tiles;
+        splitk = (int)std::max(1LL, std::min(want, (long long)nchunks / 4));
+    }
+    const int per = (nchunks + splitk - 1) / splitk, gz = (nchunks + per - 1) / per;
+    if (gz > 65535 || mtiles > 65535) return false;
+    CUtensorMap ma, mb;
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)s.cin, (cuuint64_t)s.w, (cuuint64_t)s.h, (cuuint64_t)s.n};
+        const cuuint64_t strides[3] = {(cuuint64_t)s.cin * 2, (cuuint64_t)s.w * s.cin * 2,
+                                       (cuuint64_t)s.h * s.w * s.cin * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)aw, (cuuint32_t)wbox, (cuuint32_t)hbox, 1};
+        if (!encode_map(&ma, x, 4, dims, strides, box, aw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B))
+            return false;
+    }
+    {
+        const cuuint64_t dims[4] = {(cuuint64_t)s.cout, (cuuint64_t)s.w, (cuuint64_t)s.h, (cuuint64_t)s.n};
+        const cuuint64_t strides[3] = {(cuuint64_t)s.cout * 2, (cuuint64_t)s.w * s.cout * 2,
+                                       (cuuint64_t)s.h * s.w * s.cout * 2};
+        const cuuint32_t box[4] = {(cuuint32_t)bw, (cuuint32_t)wbox, (cuuint32_t)hbox, 1};
+        if (!encode_map(&mb, dy, 4, dims, strides, box, bw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B))
+            return false;
+    }
+    if (cudaFuncSetAttribute(k_wgrad_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        *rc = CLB_NOP_ERR_CUDA;
+        return true;
+    }
+    const dim3 grid((unsigned)mtiles, (unsigned)ntn, (unsigned)gz);
+    k_wgrad_tma<<<grid, TC_THREADS, smem, st>>>(ma, mb, dw, db, s, aw, apt, bw, tile_n, cols, stages, per, nchunks,
+                                                ones_atom);
+    *rc = cudaGetLastError() == cudaSuccess ? CLB_NOP_OK : CLB_NOP_ERR_CUDA;
+    *bias_done = ones_atom >= 0;
     return true;
 }
 
@@ -1538,7 +1772,8 @@ bool launch_dgrad_small(const void* dy, const void* w, const void* mask, void* d
 bool launch_wgrad_small(const void* x, const void* dy, float* dw, float* db, ConvShape s, cudaStream_t st, int* rc) {
     if (s.taps != 1 || !aligned16(x)) return false;
     const long long npix = (long long)s.n * s.h * s.w;
-    const unsigned grid = (unsigned)std::min<long long>(4 * 152, (npix + 255) / 256);
+    // one block per SM: fewer partial sums to add atomically into the same few outputs
+    const unsigned grid = (unsigned)std::min<long long>(sm_count(), (npix + 255) / 256);
     const __nv_bfloat16 *xb = (const __nv_bfloat16*)x, *dyb = (const __nv_bfloat16*)dy;
     if (s.cout == 4 && s.cin == 8) k_wgrad_small<8, 4><<<grid, 256, 0, st>>>(xb, dyb, dw, db, npix);
     else if (s.cout == 4 && s.cin == 16) k_wgrad_small<16, 4><<<grid, 256, 0, st>>>(xb, dyb, dw, db, npix);
@@ -1587,6 +1822,11 @@ extern "C" int clb_nop_conv_wgrad_bias(const void* x, const void* dy, float* dw,
     const ConvShape s{n, h, wd, cin, cout, taps};
     const cudaStream_t st = (cudaStream_t)stream;
     int rc;
+    bool bias_done = false;
+    if (launch_wgrad_tma(x, dy, dw, db, s, splitk, st, &rc, &bias_done)) {
+        if (rc != CLB_NOP_OK || !db || bias_done) return rc;
+        return clb_nop_bias_grad(dy, db, (int64_t)n * h * wd, cout, stream);
+    }
     if (launch_wgrad_tc(x, dy, dw, db, s, splitk, st, &rc) || launch_wgrad_small(x, dy, dw, db, s, st, &rc)) return rc;
     if (db) {   // the generic paths: bias gradient in its own pass
         rc = clb_nop_bias_grad(dy, db, (int64_t)n * h * wd, cout, stream);
