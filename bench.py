@@ -65,13 +65,13 @@ BYTES_PER_CCU_F64 = 28 * 8 + 8
 # step kernel (dadd + dmul + 2 dfma per launch / nodes, ncu instruction
 # counters of the current kernel), and its FP64 pipe instructions (dadd +
 # dmul + dfma) per node.
-FP64_FLOP_PER_CCU = 261.5
-FP64_INST_PER_CCU = 179.4
+FP64_FLOP_PER_CCU = 257.5
+FP64_INST_PER_CCU = 175.4
 # DRAM bytes (read + write) per node of one launch of the current FP64 step
 # kernel, ncu on the 2048^2 case of the same workload, scaled by the node
 # count (traffic grows with the nodes): 14 + 14 values and the 64-byte
 # per-node constant table.
-DRAM_BYTES_PER_CCU_MEASURED = 280.4
+DRAM_BYTES_PER_CCU_MEASURED = 282.7
 SMS, DFMA_PER_CLK_PER_SM = 152, 2   # GB300 FP64 pipe: 2 DFMA/clk/SM (1.25 TFLOP/s at 2.07 GHz)
 
 
@@ -355,7 +355,7 @@ def batched_form(clb, torch, args, hbm_peak, src):
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                         "bytes_per_ccu": bpn,
                         "traffic": BATCH_DRAM_PER_NODE * nodes if BATCH_DRAM_PER_NODE else None,
-                        "kernel": "k_step_batch / k_step_batch_persist <StoreH16N>",
+                        "kernel": "k_step_batch_int + k_step_batch_edge (graph) / k_step_batch_persist <StoreH16N>",
                         "peak_source": f"{src} hbm_gbs"}}
     if args.no_batch_check:
         return out

@@ -1278,7 +1278,9 @@ bool launch_wgrad_tma(const void* x, const void* dy, float* dw, float* db, ConvS
     }
     const long long npix = (long long)s.n * s.h * s.w;
     if (npix * (s.cin > s.cout ? s.cin : s.cout) * s.taps >= 2147483647LL) return false;
-    const int aw = s.cin <= 32 ? 32 : 64, apt = (s.cin + aw - 1) / aw, atoms = s.taps * apt;
+    // 32-channel atoms unless 64-channel ones waste no more rows (fewer boxes)
+    const int aw = (s.cin + 31) / 32 * 32 < (s.cin + 63) / 64 * 64 ? 32 : 64;
+    const int apt = (s.cin + aw - 1) / aw, atoms = s.taps * apt;
     const int a_atoms = TC_M / aw;
     const int bw = s.cout <= 32 ? 32 : 64, batoms_all = (s.cout + bw - 1) / bw;
     const int b_atoms = std::min(batoms_all, 256 / bw), tile_n = b_atoms * bw;
@@ -1293,8 +1295,9 @@ bool launch_wgrad_tma(const void* x, const void* dy, float* dw, float* db, ConvS
     const int nchunks = (int)(npix / WG_K);
     const long long tiles = (long long)mtiles * ntn;
     if (splitk < 1) {
-        // automatic: about three CTAs per SM, each with at least 4 chunks
-        const long long want = (3LL * sm_count() + tiles - 1) / tiles;
+        // automatic: one wave of two CTAs per SM (the shared-memory limit), each
+        // with at least 4 chunks
+        const long long want = std::max(1LL, 2LL * sm_count() / tiles);
         splitk = (int)std::max(1LL, std::min(want, (long long)nchunks / 4));
     }
     const int per = (nchunks + splitk - 1) / splitk, gz = (nchunks + per - 1) / per;
