@@ -260,7 +260,7 @@ FORMS = {  # storage form -> (precision code, algorithmic bytes per coupled cell
 # DRAM bytes (read + write) per node of one launch of the current FP16 step
 # kernels, ncu on the 4096^2 case of the same workload; traffic grows with
 # the node count.  None: not captured for the kernel as it stands.
-FORMS_DRAM_PER_NODE = {"f16n": None, "f16s": None}
+FORMS_DRAM_PER_NODE = {"f16n": 75.8, "f16s": 59.7}
 # DRAM bytes (read + write) per node of one launch of the current batch
 # kernel on the 512-case workload (ncu); None: not captured for this kernel.
 BATCH_DRAM_PER_NODE = None

@@ -383,17 +383,18 @@ static void launch_step(clb_handle* h, cudaStream_t s) {
 
 template <class P, typename K>
 static void macros_as(clb_handle* h, const AuxT<typename P::R>& A, const K& kp, double* r, double* u, double* v,
-                      double* T) {
+                      double* T, unsigned long long* bad) {
     using S = typename P::S;
     const BufT<S> in = h->buf<S>(h->par);
-    if (h->prm.forchheimer) k_macros<P, true><<<h->grid, h->block, 0, h->stream>>>(in, A, kp, r, u, v, T);
-    else k_macros<P, false><<<h->grid, h->block, 0, h->stream>>>(in, A, kp, r, u, v, T);
+    if (h->prm.forchheimer) k_macros<P, true><<<h->grid, h->block, 0, h->stream>>>(in, A, kp, r, u, v, T, bad);
+    else k_macros<P, false><<<h->grid, h->block, 0, h->stream>>>(in, A, kp, r, u, v, T, bad);
 }
 
-static void launch_macros(clb_handle* h, double* r, double* u, double* v, double* T) {
-    if (h->prec == CLB_F16S) macros_as<StoreH16>(h, h->aux32(), h->k32, r, u, v, T);
-    else if (h->prec == CLB_F16N) macros_as<StoreH16N>(h, h->aux32(), h->k32, r, u, v, T);
-    else macros_as<StoreF64>(h, h->aux64(), h->k64, r, u, v, T);
+static void launch_macros(clb_handle* h, double* r, double* u, double* v, double* T,
+                          unsigned long long* bad = nullptr) {
+    if (h->prec == CLB_F16S) macros_as<StoreH16>(h, h->aux32(), h->k32, r, u, v, T, bad);
+    else if (h->prec == CLB_F16N) macros_as<StoreH16N>(h, h->aux32(), h->k32, r, u, v, T, bad);
+    else macros_as<StoreF64>(h, h->aux64(), h->k64, r, u, v, T, bad);
 }
 
 template <class P, typename K>
@@ -700,19 +701,22 @@ extern "C" int clb_macros(clb_handle* h, double* rho, double* ux, double* uy, do
     if (!h) return CLB_ERR_ARG;
     const long long n = (long long)h->prm.nx * h->prm.ny;
     double* d = h->scratch;
-    launch_macros(h, d, d + n, d + 2 * n, d + 3 * n);
+    // finiteness is checked on the device (the first bad node's index), not by
+    // scanning the copies on the host
+    unsigned long long* bad = reinterpret_cast<unsigned long long*>(h->result + 7);
+    CK(h, cudaMemsetAsync(bad, 0xFF, sizeof *bad, h->stream));
+    launch_macros(h, d, d + n, d + 2 * n, d + 3 * n, bad);
     CK(h, cudaGetLastError());
     double* outs[4] = {rho, ux, uy, T};
     for (int k = 0; k < 4; ++k)
         if (outs[k])
             CK(h, cudaMemcpyAsync(outs[k], d + k * n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaMemcpyAsync(h->host_res + 7, bad, sizeof *bad, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (const int rc = tma_status(h)) return rc;
-    for (int k = 0; k < 4; ++k)
-        if (outs[k])
-            for (long long i = 0; i < n; ++i)
-                if (!std::isfinite(outs[k][i]))
-                    return fail(h, CLB_ERR_UNSTABLE, "clb_macros: non-finite value at node %lld", i);
+    unsigned long long first;
+    std::memcpy(&first, h->host_res + 7, sizeof first);
+    if (first != ~0ULL) return fail(h, CLB_ERR_UNSTABLE, "clb_macros: non-finite value at node %llu", first);
     return CLB_OK;
 }
 

@@ -1658,11 +1658,12 @@ __global__ void __launch_bounds__(128, CLB_BATCH_MINB)
     }
 }
 
-// Macroscopic fields at the current time level (dense ny*nx FP64 outputs).
+// Macroscopic fields at the current time level (dense ny*nx FP64 outputs),
+// and (bad not NULL) the first node whose fields are not all finite.
 template <class P, bool FORCH>
 __global__ void k_macros(const BufT<typename P::S> in, const AuxT<typename P::R> A,
                          const KParamsT<typename P::R> K, double* __restrict__ orho, double* __restrict__ oux,
-                         double* __restrict__ ouy, double* __restrict__ oT) {
+                         double* __restrict__ ouy, double* __restrict__ oT, unsigned long long* __restrict__ bad) {
     using R = typename P::R;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -1676,6 +1677,9 @@ __global__ void k_macros(const BufT<typename P::S> in, const AuxT<typename P::R>
     if (oux) oux[n] = (double)X;
     if (ouy) ouy[n] = (double)Y;
     if (oT) oT[n] = (double)T;
+    // the smallest index of a node with a non-finite value (bad starts at ~0)
+    if (bad && !(isfinite((double)rho) && isfinite((double)X) && isfinite((double)Y) && isfinite((double)T)))
+        atomicMin(bad, (unsigned long long)n);
 }
 
 // Post-collision buffers whose pull reproduces the local equilibria of the
