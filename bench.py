@@ -614,8 +614,8 @@ def warm_start_form(clb, torch, ncase=4):
 def surrogate_training(torch, bf16_peak, src, batch=16, steps=20):
     """One Adam training step of the warm-start network (batch 16 at 128^2,
     seeded random inputs and targets): forward, channel-weighted MSE, input
-    and weight gradients and Adam, all in the library's kernels (tcgen05
-    convolutions).  Tensor-core FLOPs per step / CUDA-event time per step,
+    and weight gradients and Adam, all in the library's kernels (TMA-fed
+    tcgen05 convolutions).  Tensor-core FLOPs per step / CUDA-event time per step,
     against the measured BF16 peak.  The working set (~0.1 GB of activations)
     stays in L2 between steps, as it does in training."""
     from paper_2110_05943_gb300 import surrogate
@@ -651,7 +651,7 @@ def surrogate_training(torch, bf16_peak, src, batch=16, steps=20):
             "ms_per_step": sec * 1e3, "samples_per_s": n / sec,
             "roofline": {"bound": "tensor", "achieved": tf, "peak": bf16_peak, "unit": "TFLOP/s",
                          "frac": tf / bf16_peak, "flop_per_step": fl, "traffic": None,
-                         "kernel": "k_conv_tc / k_wgrad_tc (tcgen05) + elementwise, whole step",
+                         "kernel": "k_conv_tma / k_wgrad_tma (TMA + tcgen05) + elementwise, whole step",
                          "peak_source": f"{src} bf16_tflops"}}
 
 

@@ -796,11 +796,21 @@ struct StoreH16T {
         const float p = __ldg(A.phi + y * K.g.nx + x);
         return coef_from_phi<FORCH>(p, recip(p), A.ayg[y], K);
     }
+    // per node, then packed: for this form the packed version measured 3 %
+    // slower (more registers live across the pull)
     template <bool FORCH>
     static __device__ __forceinline__ CoefT<f2> coef2(const AuxT<R>& A, const KParamsT<R>& K, int x0, int y) {
-        const float* q = A.phi + y * K.g.nx + x0;
-        const f2 p = f2::make(__ldg(q), __ldg(q + 1));
-        return coef2_from_phi<FORCH>(p, recip(p), A.ayg[y], K);
+        const CoefT<float> a = coef<FORCH>(A, K, x0, y), b = coef<FORCH>(A, K, x0 + 1, y);
+        CoefT<f2> c;
+        c.ip = f2::make(a.ip, b.ip);
+        c.l0 = f2::make(a.l0, b.l0);
+        c.l0sq = f2::make(a.l0sq, b.l0sq);
+        c.aux = f2::make(a.aux, b.aux);
+        c.hdar = f2::make(a.hdar, b.hdar);
+        c.hgx = f2::make(a.hgx, b.hgx);
+        c.hgb = f2::make(a.hgb, b.hgb);
+        c.hgy = f2::make(a.hgy, b.hgy);
+        return c;
     }
     // Two interior nodes (x0, x0 + 1), x0 even, neither at the periodic x
     // seam: node x0 + 1 pulls from the offsets of node x0 plus one.
@@ -1699,7 +1709,9 @@ __global__ void k_set_fields(const BufT<typename P::S> out, const AuxT<typename 
     const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
     R f[9], g[5];
-#pragma unroll 1
+    // unrolled: each direction keeps one component of its neighbour's
+    // equilibria, and the compiler drops the other eight (and four)
+#pragma unroll
     for (int i = 0; i < 9; ++i) {
         int zx = x + ex[i], zy = y + ey[i];
         if (zx < 0 || zx >= K.g.nx) zx = K.g.wall_x ? x : wrap_hi(wrap_lo(zx, K.g.nx), K.g.nx);
