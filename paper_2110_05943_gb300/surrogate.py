@@ -161,26 +161,54 @@ def peclet(vscale: float, nu: float, Pr: float, L: float) -> float:
 
 
 # ------------------------------------------------------------------ layers
-class Conv:
-    """One convolution: FP32 master weights [taps * cin][cout], BF16 copy,
-    FP32 bias, gradients and Adam moments."""
+# Activations carry their channels padded with zeros to multiples of 32: the
+# TMA-fed convolutions copy 32- or 64-channel boxes, and a box that runs past
+# the last channel (24 of 32, say) is filled by the hardware at a large cost
+# (a 24 -> 24 layer at 16 x 128^2 takes 55 us, a 32 -> 32 one 27 us).  The
+# padding weights and biases are zero and stay zero (their gradients are
+# exactly zero), so the padded network computes the same function as the
+# real one; saved weights hold the real parts only.
+def _pad32(c: int) -> int:
+    return (c + 31) // 32 * 32
 
-    def __init__(self, torch, cin, cout, taps, relu, rng):
-        self.cin, self.cout, self.taps, self.relu = cin, cout, taps, relu
-        fan = taps * cin
+
+class Conv:
+    """One convolution: FP32 master weights [taps * cin][cout] (cin, cout
+    padded), BF16 copy and its transpose, FP32 bias, gradients and Adam
+    moments.  rin: the padded positions of the real input channels;
+    cout_real: the real outputs (the first ones)."""
+
+    def __init__(self, torch, rin, cin, cout_real, taps, relu, rng, pad_out=True):
+        self._torch = torch
+        self.rin = np.asarray(list(rin), dtype=np.int64)
+        self.cin_real, self.cout_real = len(self.rin), cout_real
+        self.cin, self.cout, self.taps, self.relu = cin, (_pad32(cout_real) if pad_out else cout_real), taps, relu
+        fan = taps * self.cin_real
         std = math.sqrt((2.0 if relu else 1.0) / fan)
-        w = rng.standard_normal((taps * cin, cout)).astype(np.float32) * std
+        w = self.embed(rng.standard_normal((taps * self.cin_real, cout_real)).astype(np.float32) * std)
         dev = "cuda"
         self.w = torch.from_numpy(w).to(dev)
         self.wb = torch.empty(w.shape, dtype=torch.bfloat16, device=dev)
-        self.b = torch.zeros(cout, dtype=torch.float32, device=dev)
+        self.b = torch.zeros(self.cout, dtype=torch.float32, device=dev)
         self.gw = torch.zeros_like(self.w)
         self.gb = torch.zeros_like(self.b)
         self.mw, self.vw = torch.zeros_like(self.w), torch.zeros_like(self.w)
         self.mb, self.vb = torch.zeros_like(self.b), torch.zeros_like(self.b)
-        self.wbt = torch.empty((cout, taps * cin), dtype=torch.bfloat16, device=dev)   # for the tcgen05 forward
+        self.wbt = torch.empty((self.cout, taps * cin), dtype=torch.bfloat16, device=dev)   # for the forward
         _ok(_lib().clb_nop_cast_bf16(_p(self.w), _p(self.wb), self.w.numel(), None), "cast")
         self.refresh_t()
+
+    def embed(self, real: np.ndarray) -> np.ndarray:
+        """[taps * cin_real][cout_real] -> the padded [taps * cin][cout], zeros elsewhere."""
+        out = np.zeros((self.taps, self.cin, self.cout), dtype=real.dtype)
+        out[:, self.rin, :self.cout_real] = real.reshape(self.taps, self.cin_real, self.cout_real)
+        return out.reshape(self.taps * self.cin, self.cout)
+
+    def real(self, t):
+        """The real part [taps * cin_real][cout_real] of a padded weight-shaped tensor."""
+        idx = self._torch.as_tensor(self.rin, device=t.device)
+        v = t.reshape(self.taps, self.cin, self.cout)[:, idx, :self.cout_real]
+        return v.reshape(self.taps * self.cin_real, self.cout_real)
 
     def refresh_t(self):
         """Rebuild the transposed BF16 copy from the BF16 weights."""
@@ -188,7 +216,7 @@ class Conv:
 
     @property
     def nparams(self):
-        return self.w.numel() + self.b.numel()
+        return self.taps * self.cin_real * self.cout_real + self.cout_real
 
 
 @dataclass
@@ -201,11 +229,18 @@ class Net:
     def create(cls, torch, seed=0, width=(24, 48, 96, 192), cin=N_IN, cout=N_OUT):
         rng = np.random.default_rng(seed)
         c1, c2, c3, c4 = width
-        spec = [(cin, c1), (c1, c1), (c1, c2), (c2, c2), (c2, c3), (c3, c3), (c3, c4), (c4, c4),
-                (c4 + c3, c3), (c3, c3), (c3 + c2, c2), (c2, c2), (c2 + c1, c1), (c1, c1)]
-        layers = [Conv(torch, a, b, 9, True, rng) for a, b in spec]
-        layers.append(Conv(torch, c1, cout, 1, False, rng))
+        P = _pad32
+        r = lambda c: range(c)
+        cat = lambda a, b: list(range(a)) + [P(a) + j for j in range(b)]   # [up(a) | skip(b)], each padded
+        spec = [(r(cin), P(cin), c1), (r(c1), P(c1), c1), (r(c1), P(c1), c2), (r(c2), P(c2), c2),
+                (r(c2), P(c2), c3), (r(c3), P(c3), c3), (r(c3), P(c3), c4), (r(c4), P(c4), c4),
+                (cat(c4, c3), P(c4) + P(c3), c3), (r(c3), P(c3), c3), (cat(c3, c2), P(c3) + P(c2), c2),
+                (r(c2), P(c2), c2), (cat(c2, c1), P(c2) + P(c1), c1), (r(c1), P(c1), c1)]
+        layers = [Conv(torch, ri, ci, co, 9, True, rng) for ri, ci, co in spec]
+        layers.append(Conv(torch, r(c1), P(c1), cout, 1, False, rng, pad_out=False))
         net = cls(layers, torch)
+        net.n_in = cin
+        net._zeros = {}
         net._flat_grads()
         return net
 
@@ -241,7 +276,7 @@ class Net:
         (all layers but the first) and weight gradient of every convolution."""
         tot = 0
         for i, (l, d) in enumerate(zip(self.layers, self.RES)):
-            one = 2.0 * n * (h // d) * (w // d) * l.taps * l.cin * l.cout
+            one = 2.0 * n * (h // d) * (w // d) * l.taps * l.cin_real * l.cout_real   # real channels
             tot += one * (2 if i == 0 else 3)
         return tot
 
@@ -268,11 +303,23 @@ class Net:
         _ok(_lib().clb_nop_concat(_p(a), _p(b), _p(y), npix, ca, cb, 0, None), "concat")
         return y
 
+    def _pad_input(self, x, n, h, w):
+        """(n, h, w, 8) -> (n, h, w, 32): the features and zero channels."""
+        t, npix = self.torch, n * h * w
+        pad = self.layers[0].cin - self.n_in
+        z = self._zeros.get(npix)
+        if z is None:
+            z = self._zeros[npix] = t.zeros((npix, pad), dtype=t.bfloat16, device="cuda")
+        y = t.empty((n, h, w, self.layers[0].cin), dtype=t.bfloat16, device="cuda")
+        _ok(_lib().clb_nop_concat(_p(x), _p(z), _p(y), npix, self.n_in, pad, 0, None), "pad")
+        return y
+
     def forward(self, x, n, h, w):
         """x: (n, h, w, 8) BF16 device tensor -> (n, h, w, 4) FP32, plus the
-        activations the backward pass needs."""
+        activations the backward pass needs (channels padded to multiples of 32)."""
         L = self.layers
         c1, c2, c3, c4 = L[0].cout, L[2].cout, L[4].cout, L[6].cout
+        x = self._pad_input(x, n, h, w)
         A = {"x": x}
         A[1] = self._conv(L[0], x, n, h, w)
         A[2] = self._conv(L[1], A[1], n, h, w)
@@ -303,10 +350,18 @@ class Net:
     # ---- backward
     def _grads(self, l, x, dy, n, h, w, mask, want_dx=True):
         """Accumulate l's weight and bias gradients; return dx (BF16) masked
-        by `mask` > 0 (the ReLU of the layer that produced x) if given."""
+        by `mask` > 0 (the ReLU of the layer that produced x) if given.  The
+        weight gradient, which nothing before the optimiser step needs, runs
+        on a side stream, overlapping the input-gradient chain of the
+        default stream."""
         lib, t = _lib(), self.torch
-        _ok(lib.clb_nop_conv_wgrad_bias(_p(x), _p(dy), _p(l.gw), _p(l.gb), n, h, w, l.cin, l.cout, l.taps, 0, None),
-            "wgrad")
+        ev = t.cuda.Event()
+        ev.record(t.cuda.default_stream())
+        self._ws.wait_event(ev)
+        _ok(lib.clb_nop_conv_wgrad_bias(_p(x), _p(dy), _p(l.gw), _p(l.gb), n, h, w, l.cin, l.cout, l.taps, 0,
+                                        _VP(self._ws.cuda_stream)), "wgrad")
+        x.record_stream(self._ws)
+        dy.record_stream(self._ws)
         if not want_dx:
             return None
         dx = t.empty((n, h, w, l.cin), dtype=t.bfloat16, device="cuda")
@@ -329,6 +384,8 @@ class Net:
     def backward(self, dout, A, n, h, w):
         L, t, lib = self.layers, self.torch, _lib()
         c1, c2, c3, c4 = L[0].cout, L[2].cout, L[4].cout, L[6].cout
+        if getattr(self, "_ws", None) is None:
+            self._ws = t.cuda.Stream()
         _ok(lib.clb_nop_zero(_p(self.grads), self.grads.numel() * 4, None), "zero")
         h2, w2, h4, w4, h8, w8 = h // 2, w // 2, h // 4, w // 4, h // 8, w // 8
         d = self._grads(L[14], A[14], dout, n, h, w, A[14])
@@ -361,6 +418,9 @@ class Net:
         _ok(lib.clb_nop_pool2(_p(dp1), _p(d2), n, h, w, c1, 1, None), "pool_bwd")
         d = self._grads(L[1], A[1], self._add_mask(d2, d2_skip, A[2]), n, h, w, A[1])
         self._grads(L[0], A["x"], d, n, h, w, None, want_dx=False)
+        done = t.cuda.Event()                 # the optimiser step waits for every weight gradient
+        done.record(self._ws)
+        t.cuda.default_stream().wait_event(done)
 
     def adam(self, step, lr, b1=0.9, b2=0.999, eps=1e-8):
         # one launch: every layer's weights (BF16 copy and its transpose refreshed) and biases
@@ -377,14 +437,15 @@ class Net:
         return loss, g
 
     def state(self):
-        return [(l.w.cpu().numpy(), l.b.cpu().numpy()) for l in self.layers]
+        """Real weights [taps * cin][cout] and biases of every layer (FP32)."""
+        return [(l.real(l.w).cpu().numpy(), l.b[:l.cout_real].cpu().numpy()) for l in self.layers]
 
     def save(self, path):
-        """Weights as BF16 bit patterns (what inference uses) and FP32 biases."""
+        """Real weights as BF16 bit patterns (what inference uses) and FP32 biases."""
         arrs = {"scale_coef": np.asarray(self.scale_coef if self.scale_coef is not None else [], dtype=np.float64)}
         for i, l in enumerate(self.layers):
-            arrs[f"w{i}"] = l.wb.view(self.torch.int16).cpu().numpy()
-            arrs[f"b{i}"] = l.b.cpu().numpy()
+            arrs[f"w{i}"] = l.real(l.wb).contiguous().view(self.torch.int16).cpu().numpy()
+            arrs[f"b{i}"] = l.b[:l.cout_real].cpu().numpy()
         np.savez_compressed(path, **arrs)
 
     def load(self, path):
@@ -392,12 +453,14 @@ class Net:
         t = self.torch
         self.scale_coef = z["scale_coef"] if len(z["scale_coef"]) else None
         for i, l in enumerate(self.layers):
-            wb = t.from_numpy(z[f"w{i}"]).to("cuda").view(t.bfloat16)
-            if wb.shape != l.wb.shape:
-                raise ValueError(f"layer {i}: stored shape {tuple(wb.shape)} != {tuple(l.wb.shape)}")
-            l.wb.copy_(wb)
-            l.w.copy_(wb.float())
-            l.b.copy_(t.from_numpy(z[f"b{i}"]).to("cuda"))
+            real = (l.taps * l.cin_real, l.cout_real)
+            if z[f"w{i}"].shape != real:
+                raise ValueError(f"layer {i}: stored shape {z[f'w{i}'].shape} != {real}")
+            wr = t.from_numpy(z[f"w{i}"]).view(t.bfloat16).float().numpy()
+            l.w.copy_(t.from_numpy(l.embed(wr)).to("cuda"))     # BF16 values, exact in FP32
+            _ok(_lib().clb_nop_cast_bf16(_p(l.w), _p(l.wb), l.w.numel(), None), "cast")
+            l.b.zero_()
+            l.b[:l.cout_real].copy_(t.from_numpy(z[f"b{i}"]).to("cuda"))
             l.refresh_t()
         return self
 

@@ -260,13 +260,14 @@ def test_adam_multi_matches_the_single_tensor_step(lib):
 
 
 class _RefNet(torch.nn.Module):
-    """The surrogate's architecture in plain PyTorch FP32, weights copied in."""
+    """The surrogate's architecture in plain PyTorch FP32 with its real
+    (unpadded) channel counts, the real parts of the weights copied in."""
 
     def __init__(self, net):
         super().__init__()
-        self.w = [torch.nn.Parameter(l.wb.float().cpu().clone()) for l in net.layers]
-        self.b = [torch.nn.Parameter(l.b.cpu().clone()) for l in net.layers]
-        self.spec = [(l.cin, l.cout, l.taps, l.relu) for l in net.layers]
+        self.w = [torch.nn.Parameter(l.real(l.wb).float().cpu().clone()) for l in net.layers]
+        self.b = [torch.nn.Parameter(l.b[:l.cout_real].cpu().clone()) for l in net.layers]
+        self.spec = [(l.cin_real, l.cout_real, l.taps, l.relu) for l in net.layers]
 
     def conv(self, i, x):
         cin, cout, taps, relu = self.spec[i]
@@ -314,8 +315,38 @@ def test_network_forward_backward_matches_autograd(lib):
     assert _rel_l2(out.cpu(), o.detach()) < 2e-2
     assert abs(loss.item() / lref.item() - 1) < 2e-2
     for i, l in enumerate(net.layers):
-        assert _rel_l2(l.gw.cpu(), ref.w[i].grad) < 6e-2, i
-        assert _rel_l2(l.gb.cpu(), ref.b[i].grad) < 6e-2, i
+        assert _rel_l2(l.real(l.gw).cpu(), ref.w[i].grad) < 6e-2, i
+        assert _rel_l2(l.gb[:l.cout_real].cpu(), ref.b[i].grad) < 6e-2, i
+        # the channel padding stays inert: its weights, biases and gradients are exactly zero
+        gw = l.gw.clone().reshape(l.taps, l.cin, l.cout)
+        gw[:, torch.as_tensor(l.rin, device=gw.device), :l.cout_real] = 0
+        assert torch.count_nonzero(gw).item() == 0 and torch.count_nonzero(l.gb[l.cout_real:]).item() == 0, i
+        wz = l.wb.float().clone().reshape(l.taps, l.cin, l.cout)
+        wz[:, torch.as_tensor(l.rin, device=wz.device), :l.cout_real] = 0
+        assert torch.count_nonzero(wz).item() == 0, i
+
+
+def test_weights_round_trip_and_committed_weights_load(lib, tmp_path):
+    """Saved weights are the real parts; loading them into a fresh (padded)
+    network restores the same function.  The committed warm-start weights
+    load into the current network."""
+    import os
+    from paper_2110_05943_gb300 import surrogate
+    a = surrogate.Net.create(torch, seed=7)
+    path = str(tmp_path / "w.npz")
+    a.scale_coef = np.arange(9.0)
+    a.save(path)
+    b = surrogate.Net.create(torch, seed=8).load(path)
+    for la, lb in zip(a.layers, b.layers):   # the BF16 weights inference uses, and the biases
+        assert torch.equal(la.real(la.wb), lb.real(lb.wb)) and torch.equal(la.b, lb.b)
+        assert torch.equal(lb.w, lb.wb.float())
+    x = _bf((2, 16, 16, surrogate.N_IN), 31).cuda()
+    oa, _ = a.forward(x, 2, 16, 16)
+    ob, _ = b.forward(x, 2, 16, 16)
+    assert torch.equal(oa, ob)
+    pkg = os.path.dirname(os.path.abspath(surrogate.__file__))
+    c = surrogate.Net.create(torch, seed=0).load(os.path.join(pkg, "weights", "warmstart_128.npz"))
+    assert c.scale_coef is not None and c.nparams == a.nparams
 
 
 def test_training_reduces_the_loss(lib):
