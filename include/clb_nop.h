@@ -13,11 +13,14 @@
  * (cudaStream_t, NULL = legacy stream) and returns CLB_NOP_OK or an error;
  * shapes are checked on the host before any launch.  Products run on the
  * BF16 tensor cores with FP32 accumulation, on tcgen05 (accumulator in
- * TMEM): the forward and input-gradient convolutions whenever the gathered
- * operand's channel count is a multiple of 8 and the operands are 16-byte
- * aligned (for the forward pass: when the transposed weights are given),
- * the weight gradient whenever cin and cout are multiples of 8 and x, dy
- * are 16-byte aligned; other shapes run on an mma.sync implicit GEMM.
+ * TMEM): fed by TMA copies when the pixels tile into whole image rows and
+ * the channel counts are multiples of 8 (for the forward pass: when the
+ * transposed weights are given), otherwise from operands gathered through
+ * registers when the gathered channel count is a multiple of 8 and the
+ * operands are 16-byte aligned; the 1x1 convolution to 4 outputs runs on
+ * CUDA cores; other shapes on an mma.sync implicit GEMM.  A TMA box that
+ * extends past a tensor's last channel is much slower than one inside it:
+ * channel counts that are multiples of 32 keep every box inside.
  */
 #ifndef CLB_NOP_H
 #define CLB_NOP_H

@@ -5,13 +5,21 @@
 //
 // Layout: activations NHWC (channels fastest), BF16.  Convolution weights
 // as a [taps * Cin][Cout] matrix (Cout fastest), taps = 9 (3x3) or 1 (1x1).
-// Every convolution pass is an implicit GEMM on the BF16 tensor cores
-// (mma.sync m16n8k16, FP32 accumulate): 64 x 64 output tiles, 32-deep K
-// chunks, four warps of 32 x 32, operands gathered into shared memory with
-// zero fill at image borders and tile tails.
+// Every convolution pass is an implicit GEMM on the BF16 tensor cores with
+// FP32 accumulation:
 //   forward : Y[p, co]   = sum_{tap, ci} X[p + d(tap), ci] W[tap, ci, co] (+ b, ReLU)
 //   dgrad   : dX[p, ci]  = sum_{tap, co} dY[p - d(tap), co] W[tap, ci, co]
 //   wgrad   : dW[tap, ci, co] += sum_p X[p + d(tap), ci] dY[p, co]   (split K, FP32 atomics)
+// In order of preference (the first that takes the shape runs):
+//   k_conv_tma / k_wgrad_tma -- operands brought by TMA from the NHWC tensors
+//     into swizzled shared memory, tcgen05.mma with the accumulator in TMEM
+//     (whole-row pixel tiles, channel counts multiples of 8);
+//   k_conv_tc / k_wgrad_tc   -- the same MMAs with operands gathered by all
+//     threads through registers (any width);
+//   k_wgrad_small / k_dgrad_small -- CUDA cores, the 1x1 head (4 outputs);
+//   k_conv_gemm              -- mma.sync m16n8k16, 64 x 64 output tiles,
+//     operands gathered with zero fill at image borders and tile tails (any
+//     channel count).
 #include <cuda.h>           // CUtensorMap and its enums (the encoder is fetched at run time)
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
