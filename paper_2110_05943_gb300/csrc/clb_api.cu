@@ -368,10 +368,17 @@ static void step2_as(clb_handle* h, cudaStream_t s, long long limit = TT_LIMIT, 
     const int threads = (int)(h->block2.x * h->block2.y);
     const unsigned nb = (unsigned)(nt + (edge_count(G) + threads - 1) / threads);
     if (nb == 0) return;
-    if (sh && fo) k_step2<P, true, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
-    else if (sh) k_step2<P, true, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
-    else if (fo) k_step2<P, false, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
-    else k_step2<P, false, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt, outer);
+    if (outer) {
+        if (sh && fo) k_step2<P, true, true, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+        else if (sh) k_step2<P, true, false, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+        else if (fo) k_step2<P, false, true, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+        else k_step2<P, false, false, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+    } else {
+        if (sh && fo) k_step2<P, true, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+        else if (sh) k_step2<P, true, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+        else if (fo) k_step2<P, false, true><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+        else k_step2<P, false, false><<<nb, h->block2, 0, s>>>(in, out, A, h->k32, tx, nt);
+    }
 }
 
 static void launch_step(clb_handle* h, cudaStream_t s) {

@@ -162,17 +162,12 @@ struct Dither {
     uint32_t h0, h1;   // value k uses the word h0 + k h1
 };
 
-// Per-step part of the hash (one per launch, not per node).
-CLB_HD uint32_t seq_hash(uint32_t seq) { return mix32(seq + 0x632BE5ABU); }
-
-CLB_HD Dither dither_hashed(uint32_t node, uint32_t sh) {
+CLB_HD Dither dither_for(uint32_t node, uint32_t seq) {
     Dither d;
-    d.h0 = mix32(node * 0x9E3779B1U ^ sh);
+    d.h0 = mix32(node * 0x9E3779B1U ^ mix32(seq + 0x632BE5ABU));
     d.h1 = ((d.h0 ^ (d.h0 >> 15)) * 0x85EBCA77U) | 1U;
     return d;
 }
-
-CLB_HD Dither dither_for(uint32_t node, uint32_t seq) { return dither_hashed(node, seq_hash(seq)); }
 
 CLB_HD uint32_t dword(const Dither& d, int k) { return d.h0 + (uint32_t)k * d.h1; }
 
@@ -838,9 +833,9 @@ struct StoreH16T {
     }
     static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
                                                   const f2 (&f)[9], const f2 (&g)[5], f2, f2, f2, f2, f2,
-                                                  uint32_t sh) {
+                                                  uint32_t seq) {
         const int o = y * K.g.px + x0, Q = (int)K.g.plane;
-        const Dither rw = dither_hashed((uint32_t)o, sh);   // one word per stored pair
+        const Dither rw = dither_for((uint32_t)o, seq);   // one word per stored pair
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const f2 d = fma(f[i], f2(kDevScale), f2(-K.wfs[i]));   // (f - w_i rho_0) 2^12
@@ -1056,7 +1051,7 @@ struct StoreH16NT {
     }
     static __device__ __forceinline__ void store2(const BufT<S>& B, const KParamsT<R>& K, int x0, int y,
                                                   const f2 (&f)[9], const f2 (&g)[5], f2 rho, f2 X, f2 Y, f2 T, f2 ip,
-                                                  uint32_t sh) {
+                                                  uint32_t seq) {
         const int o = y * K.g.px + x0, Q = (int)K.g.plane;
         // T: T - T0 in this form
         const __half2 a0 = __floats2half2_rn(rho.lo() - 1.0f, X.lo()), b0 = __floats2half2_rn(Y.lo(), T.lo());
@@ -1078,7 +1073,7 @@ struct StoreH16NT {
         const f2 ge[5] = {geqc_comp<0>(bT, bX, bY, s, c, t0), geqc_comp<1>(bT, bX, bY, s, c, t0),
                           geqc_comp<2>(bT, bX, bY, s, c, t0), geqc_comp<3>(bT, bX, bY, s, c, t0),
                           geqc_comp<4>(bT, bX, bY, s, c, t0)};
-        const Dither rw = dither_hashed((uint32_t)o, sh);   // one word per stored pair
+        const Dither rw = dither_for((uint32_t)o, seq);   // one word per stored pair
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const f2 d = (f[i] - fe[i]) * f2(kDevScale);
@@ -1350,13 +1345,12 @@ __global__ void __launch_bounds__(CLB_F64_THREADS, CLB_F64_MINB)
 // to the per-node path.
 // Macroscopic state, both collisions and the store of an interior pair
 // whose streamed values f, g (pre-collision, the form's representation)
-// have been pulled; c: the pair's constants, sh: seq_hash of the input
-// buffer's step counter.
+// have been pulled; c: the pair's constants, P2: the model parameters on
+// pairs, seq: the input buffer's step counter.
 template <class P, bool SHIFT, bool FORCH>
-__device__ __forceinline__ void collide_store_pair(f2 (&f)[9], f2 (&g)[5], const CoefT<f2>& c,
+__device__ __forceinline__ void collide_store_pair(f2 (&f)[9], f2 (&g)[5], const CoefT<f2>& c, const PhysT<f2>& P2,
                                                    const BufT<typename P::S>& out, const KParamsT<float>& K, int x0,
-                                                   int y, uint32_t sh) {
-    const PhysT<f2> P2 = splat(K.p);
+                                                   int y, uint32_t seq) {
     const Mom9T<f2> k = moments9(f);
     const f2 n0 = sum5(g);
     const f2 Tt = n0 * P2.inv_sigma;          // the form's representation of T
@@ -1367,16 +1361,17 @@ __device__ __forceinline__ void collide_store_pair(f2 (&f)[9], f2 (&g)[5], const
     collide9<f2, SHIFT>(f, k, k.rho, X, Y, hFx, hFy, c.ip, P2);
     if constexpr (P::kCentred) collide5_centred<f2, SHIFT>(g, n0, Tt, X, Y, f2(K.T0), P2);
     else collide5<f2, SHIFT>(g, n0, T, X, Y, P2);
-    P::store2(out, K, x0, y, f, g, k.rho, X, Y, Tt, c.ip, sh);
+    P::store2(out, K, x0, y, f, g, k.rho, X, Y, Tt, c.ip, seq);
 }
 
 template <class P, bool SHIFT, bool FORCH>
 __device__ __forceinline__ void step_pair_interior(const BufT<typename P::S>& in, const BufT<typename P::S>& out,
                                                    const AuxT<float>& A, const KParamsT<float>& K, int x0, int y) {
+    const PhysT<f2> P2 = splat(K.p);
     const CoefT<f2> c = P::template coef2<FORCH>(A, K, x0, y);
     f2 f[9], g[5];
     P::pull2(as_const(in), A, K, x0, y, f, g);
-    collide_store_pair<P, SHIFT, FORCH>(f, g, c, out, K, x0, y, seq_hash(step_seq<typename P::Ld>(in, out, x0, y)));
+    collide_store_pair<P, SHIFT, FORCH>(f, g, c, P2, out, K, x0, y, step_seq<typename P::Ld>(in, out, x0, y));
 }
 
 // True if the pair (x0, x0 + 1) takes the packed path.
@@ -1444,19 +1439,19 @@ struct Step2MinBlocks<StoreH16T<L>> {
     static constexpr int value = 6;
 };
 
-// outer_rows: the pair tiles cover only the rows 0 and ny - 1 (thread rows 0
-// and 1 of one band of tiles), the other rows' interior pairs being taken by
-// the TMA-fed kernel.
-template <class P, bool SHIFT, bool FORCH>
+// OUTER: the pair tiles cover only the rows 0 and ny - 1 (thread rows 0 and
+// 1 of one band of tiles), the other rows' interior pairs being taken by the
+// TMA-fed kernel.
+template <class P, bool SHIFT, bool FORCH, bool OUTER = false>
 __global__ void __launch_bounds__(128, Step2MinBlocks<P>::value)
     k_step2(const BufT<typename P::S> in, const BufT<typename P::S> out,
                                                   const AuxT<float> A, const KParamsT<float> K, int tiles_x,
-                                                  int n_tiles, int outer_rows) {
+                                                  int n_tiles) {
     const int b = blockIdx.x;
     if (b < n_tiles) {
         const int x0 = 2 * ((b % tiles_x) * blockDim.x + threadIdx.x);
         int y = (b / tiles_x) * blockDim.y + threadIdx.y;
-        if (outer_rows) {
+        if constexpr (OUTER) {
             if (threadIdx.y > 1) return;
             y = threadIdx.y == 0 ? 0 : K.g.ny - 1;
         }

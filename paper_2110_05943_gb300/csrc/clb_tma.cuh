@@ -164,7 +164,8 @@ __global__ void __launch_bounds__(TT_THREADS, CLB_TT_MINB)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const uint32_t sh = seq_hash(in.seq ? __ldg(in.seq) : 0u);
+    const uint32_t seq = in.seq ? __ldg(in.seq) : 0u;
+    const PhysT<f2> P2 = splat(K.p);
     int issued = 0;
     if (tid == 0)
         for (int s = 0; s < TT_STAGES; ++s) {
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(TT_THREADS, CLB_TT_MINB)
             const float2 q = *reinterpret_cast<const float2*>(stage + TT_I_OFF + 4 * ((ly + 1) * TT_IX + lx + 4));
             const f2 ip = f2::make(q.x, q.y);
             const CoefT<f2> c = coef2_from_phi<FORCH>(recip(ip), ip, A.ayg[y], K);
-            collide_store_pair<StoreH16NT<LdNC>, SHIFT, FORCH>(f, g, c, out, K, x0, y, sh);
+            collide_store_pair<StoreH16NT<LdNC>, SHIFT, FORCH>(f, g, c, P2, out, K, x0, y, seq);
         }
         __syncthreads();   // every thread is done with stage st (and has seen s_fail)
         if (s_fail) break;
