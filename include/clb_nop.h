@@ -20,7 +20,7 @@
  * operands are 16-byte aligned; the 1x1 convolution to 4 outputs runs on
  * CUDA cores; other shapes on an mma.sync implicit GEMM.  A TMA box that
  * extends past a tensor's last channel is much slower than one inside it:
- * channel counts that are multiples of 32 keep every box inside.
+ * channel counts of 32, or multiples of 64, keep every box inside.
  */
 #ifndef CLB_NOP_H
 #define CLB_NOP_H
