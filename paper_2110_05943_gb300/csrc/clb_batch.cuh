@@ -22,6 +22,8 @@ struct clb_batch {
     int shift = 1, forch = 1;
     cudaStream_t stream = nullptr;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_side = nullptr;  // graph capture: the edge kernel's branch
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     void* table = nullptr;          // CaseT array on the device
     int4* tiles = nullptr;          // tile list on the device (all tiles; FP64 and the persistent mode)
     int ntiles = 0;
@@ -126,12 +128,33 @@ static int batch_build_tiles(clb_batch* b) {
     return rc;
 }
 
+// Captured graphs run the edge kernel as a branch parallel to the interior
+// kernel (build-time option; 0 captures the two launches in sequence).
+#ifndef CLB_BATCH_FORK
+#define CLB_BATCH_FORK 1
+#endif
+
+// One step.  With a side stream (graph capture) the edge kernel is a
+// parallel branch beside the interior kernel -- they write disjoint nodes --
+// so its few slow blocks run under the interior kernel instead of after it.
 template <class P, int NPT>
-static void batch_launch_as(clb_batch* b, cudaStream_t s) {
+static void batch_launch_as(clb_batch* b, cudaStream_t s, cudaStream_t side) {
     using C = CaseT<typename P::R, typename P::S>;
     const C* tab = (const C*)b->table;
     const dim3 block(kShapes[b->shape][0], kShapes[b->shape][1]);
     if constexpr (NPT == 2) {
+        const bool fork = side && b->n_itiles > 0 && b->n_echunks > 0;
+        cudaStream_t es = s;
+        if (fork && cudaEventRecord(b->ev_fork, s) == cudaSuccess && cudaStreamWaitEvent(side, b->ev_fork, 0) == cudaSuccess)
+            es = side;
+        if (b->n_echunks > 0) {
+            const int4* e = b->echunks;
+            const unsigned g = (unsigned)b->n_echunks;
+            if (b->shift && b->forch) k_step_batch_edge<P, true, true><<<g, 128, 0, es>>>(tab, e, b->par);
+            else if (b->shift) k_step_batch_edge<P, true, false><<<g, 128, 0, es>>>(tab, e, b->par);
+            else if (b->forch) k_step_batch_edge<P, false, true><<<g, 128, 0, es>>>(tab, e, b->par);
+            else k_step_batch_edge<P, false, false><<<g, 128, 0, es>>>(tab, e, b->par);
+        }
         if (b->n_itiles > 0) {
             const int grid = (b->n_itiles + b->per_cta - 1) / b->per_cta;
             const int4* t = b->itiles;
@@ -140,13 +163,9 @@ static void batch_launch_as(clb_batch* b, cudaStream_t s) {
             else if (b->forch) k_step_batch_int<P, false, true><<<grid, block, 0, s>>>(tab, t, b->n_itiles, b->per_cta, b->par);
             else k_step_batch_int<P, false, false><<<grid, block, 0, s>>>(tab, t, b->n_itiles, b->per_cta, b->par);
         }
-        if (b->n_echunks > 0) {
-            const int4* e = b->echunks;
-            const unsigned g = (unsigned)b->n_echunks;
-            if (b->shift && b->forch) k_step_batch_edge<P, true, true><<<g, 128, 0, s>>>(tab, e, b->par);
-            else if (b->shift) k_step_batch_edge<P, true, false><<<g, 128, 0, s>>>(tab, e, b->par);
-            else if (b->forch) k_step_batch_edge<P, false, true><<<g, 128, 0, s>>>(tab, e, b->par);
-            else k_step_batch_edge<P, false, false><<<g, 128, 0, s>>>(tab, e, b->par);
+        if (es != s) {   // join: the next step waits for both branches
+            cudaEventRecord(b->ev_join, es);
+            cudaStreamWaitEvent(s, b->ev_join, 0);
         }
     } else {
         const int grid = (b->ntiles + b->per_cta - 1) / b->per_cta;
@@ -206,11 +225,11 @@ static cudaError_t batch_persist(clb_batch* b, cudaStream_t s, int par0, int nst
     return batch_persist_as<StoreF64T<L>, 1>(b, s, par0, nsteps, extra, limit);
 }
 
-static void batch_launch(clb_batch* b, cudaStream_t s) {
+static void batch_launch(clb_batch* b, cudaStream_t s, cudaStream_t side = nullptr) {
     if (b->ntiles > 0) {
-        if (b->prec == CLB_F16S) batch_launch_as<StoreH16, 2>(b, s);
-        else if (b->prec == CLB_F16N) batch_launch_as<StoreH16N, 2>(b, s);
-        else batch_launch_as<StoreF64, 1>(b, s);
+        if (b->prec == CLB_F16S) batch_launch_as<StoreH16, 2>(b, s, side);
+        else if (b->prec == CLB_F16N) batch_launch_as<StoreH16N, 2>(b, s, side);
+        else batch_launch_as<StoreF64, 1>(b, s, side);
     }
     b->par = 1 - b->par;
 }
@@ -227,7 +246,7 @@ static cudaGraphExec_t batch_capture(clb_batch* b, int par) {
     }
     if (b->mode == CLB_BATCH_PERSISTENT) batch_persist(b, b->cap_stream, par, kGraphSteps, 0, b->wait_limit);
     else
-        for (int i = 0; i < kGraphSteps; ++i) batch_launch(b, b->cap_stream);
+        for (int i = 0; i < kGraphSteps; ++i) batch_launch(b, b->cap_stream, CLB_BATCH_FORK ? b->cap_side : nullptr);
     const cudaError_t e = cudaStreamEndCapture(b->cap_stream, &gr);
     b->par = save;
     if (e != cudaSuccess || !gr) {
@@ -294,7 +313,10 @@ extern "C" int clb_batch_init(clb_batch** out, int32_t ncase, const clb_params* 
         b->active.push_back(1);
         b->flip.push_back(0);
     }
-    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->cap_side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming) != cudaSuccess) {
         bfail(b, CLB_ERR_CUDA, "clb_batch_init: stream creation failed");
         return bail(CLB_ERR_CUDA);
     }
@@ -529,5 +551,8 @@ extern "C" void clb_batch_destroy(clb_batch* b) {
     cudaFree(b->itiles);
     cudaFree(b->echunks);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    if (b->cap_side) cudaStreamDestroy(b->cap_side);
+    if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+    if (b->ev_join) cudaEventDestroy(b->ev_join);
     delete b;
 }
