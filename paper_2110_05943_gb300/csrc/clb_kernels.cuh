@@ -1394,6 +1394,9 @@ __device__ __forceinline__ void step_pair(const BufT<typename P::S>& in, const B
 // of walled S/N rows, and in every other row the nodes of its first and its
 // last pair (all nodes of a row with fewer than three pairs).  Count and
 // the i-th one.
+#ifndef CLB_EDGE_BY_COLUMN
+#define CLB_EDGE_BY_COLUMN 1
+#endif
 __host__ __device__ inline int edge_per_row(int nx) {
     const int np = (nx + 1) / 2;
     if (np < 3) return nx;
@@ -1412,8 +1415,15 @@ __device__ __forceinline__ void edge_node(const Geo& G, long long i, int& x, int
         if (i < 2LL * G.nx) { x = (int)(i - G.nx); y = G.ny - 1; return; }
         i -= 2LL * G.nx;
     }
+#if CLB_EDGE_BY_COLUMN
+    // column by column (all rows of one edge column, then the next): a warp's
+    // nodes are then all walls or all fluid and take one branch of step_node
+    const int rows = G.wall_y ? G.ny - 2 : G.ny;
+    const int k = (int)(i / rows), r = (int)(i - (long long)k * rows);
+#else
     const int ne = edge_per_row(G.nx);
     const int r = (int)(i / ne), k = (int)(i - (long long)r * ne);
+#endif
     y = r + (G.wall_y ? 1 : 0);
     const int np = (G.nx + 1) / 2;
     x = (np < 3 || k < 2) ? k : 2 * (np - 1) + (k - 2);
