@@ -349,13 +349,14 @@ def batched_form(clb, torch, args, hbm_peak, src):
     bpn = FORMS["f16n"][1]
     gbs = bpn * rates[best] * 1e6 / 1e9
     out = {"workload": f"{len(cases)} seeded porous cavities (batch_cases seed 7), uneven grids, FP16N",
+           "cases": len(cases),
            "value": rates[best], "unit": UNIT, "mode": best, "mlups_by_mode": rates, "steps": steps,
            "nodes_per_step": nodes, "ms_per_step": nodes / (rates[best] * 1e6) * 1e3, "tile_choice": choice,
            "finite_cases": int(np.isfinite(nu).sum()),
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                         "bytes_per_ccu": bpn,
                         "traffic": BATCH_DRAM_PER_NODE * nodes if BATCH_DRAM_PER_NODE else None,
-                        "kernel": "k_step_batch_int + k_step_batch_edge (graph) / k_step_batch_persist <StoreH16N>",
+                        "kernel": "k_step_batch_mix (graph) / k_step_batch_persist <StoreH16N>",
                         "peak_source": f"{src} hbm_gbs"}}
     if args.no_batch_check:
         return out
@@ -658,7 +659,7 @@ def surrogate_training(torch, bf16_peak, src, batch=16, steps=20):
 def _summary(line):
     """Headline figures of every section, compact (the last key of the line)."""
     r3 = lambda v: None if v is None else float(f"{v:.4g}")
-    s = {"f64_4096": {"mlups": r3(line["value"]), "frac": r3(line["roofline"]["frac"]),
+    s = {f"f64_{line['config']['nx']}": {"mlups": r3(line["value"]), "frac": r3(line["roofline"]["frac"]),
                       "bound": line["roofline"]["bound"],
                       "fp64_pipe_frac": r3(line["roofline"].get("fp64_pipe_frac")),
                       "e2e_mlups": r3((line.get("e2e") or {}).get("value"))}}
@@ -672,7 +673,7 @@ def _summary(line):
             s[tag]["steps"] = a["steps"]
     b = line.get("batch")
     if b:
-        s["batch_512"] = {"mlups": r3(b["value"]), "mode": b["mode"], "hbm_frac": r3(b["roofline"]["frac"]),
+        s[f"batch_{b['cases']}"] = {"mlups": r3(b["value"]), "mode": b["mode"], "hbm_frac": r3(b["roofline"]["frac"]),
                           "by_mode": {k: r3(v) for k, v in b["mlups_by_mode"].items()},
                           "max_rel_nu_err_8": r3((b.get("validation") or {}).get("max_rel_nu_error"))}
     v = line.get("batch_validation")

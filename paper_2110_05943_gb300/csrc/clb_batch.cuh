@@ -31,6 +31,8 @@ struct clb_batch {
     int n_itiles = 0;
     int4* echunks = nullptr;        // and chunks of edge nodes (case, first edge index, count)
     int n_echunks = 0;
+    int4* work = nullptr;           // FP16 forms, one-launch steps: per block (0, first tile) or (1, edge chunk)
+    int n_work = 0;
     int64_t nodes = 0;              // active nodes per step
     int par = 0;
     int64_t t = 0;
@@ -105,6 +107,7 @@ static int batch_build_tiles(clb_batch* b) {
     const int bx = kShapes[b->shape][0], by = kShapes[b->shape][1];
     const int tw = bx * nodes_per_thread(b);
     std::vector<int4> host, inner, edges;
+    std::vector<long long> anchor;   // per edge chunk: the interior tile covering its last row (-1: none before)
     b->nodes = 0;
     for (size_t c = 0; c < b->cases.size(); ++c) {
         if (!b->active[c]) continue;
@@ -115,21 +118,57 @@ static int batch_build_tiles(clb_batch* b) {
         if (b->prec == CLB_F64) continue;
         const Geo& G = b->cases[c]->k32.g;
         const int y_lo = G.wall_y ? 1 : 0, y_hi = G.wall_y ? G.ny - 2 : G.ny - 1;
-        for (int y0 = y_lo; y0 <= y_hi; y0 += by)
-            for (int x0 = 2; x0 + 2 < G.nx; x0 += tw) inner.push_back(make_int4((int)c, x0, y0, 0));
+        const long long first = (long long)inner.size();
+        int ntx = 0, nty = 0;
+        for (int y0 = y_lo; y0 <= y_hi; y0 += by, ++nty) {
+            ntx = 0;
+            for (int x0 = 2; x0 + 2 < G.nx; x0 += tw, ++ntx) inner.push_back(make_int4((int)c, x0, y0, 0));
+        }
         const long long ne = edge_count(G);
-        for (long long i0 = 0; i0 < ne; i0 += 128)
-            edges.push_back(make_int4((int)c, (int)i0, (int)std::min(128LL, ne - i0), 0));
+        for (long long i0 = 0; i0 < ne; i0 += 128) {
+            const int cnt = (int)std::min(128LL, ne - i0);
+            edges.push_back(make_int4((int)c, (int)i0, cnt, 0));
+            int ymax = 0;
+            for (int k = 0; k < cnt; ++k) {
+                int x, y;
+                edge_node(G, i0 + k, x, y);
+                ymax = std::max(ymax, y);
+            }
+            if (ntx == 0) {
+                anchor.push_back(first - 1);
+            } else {
+                const int ty = std::min(std::max(ymax - y_lo, 0) / by, nty - 1);
+                anchor.push_back(first + (long long)ty * ntx + ntx - 1);
+            }
+        }
+    }
+    // one-launch order: each interior block, then the edge chunks anchored in it
+    std::vector<int4> work;
+    if (b->prec != CLB_F64) {
+        const int pc = b->per_cta;
+        std::vector<std::vector<int>> after((inner.size() + pc - 1) / pc + 1);   // [0]: before every block
+        for (size_t j = 0; j < edges.size(); ++j) after[anchor[j] < 0 ? 0 : anchor[j] / pc + 1].push_back((int)j);
+        for (int j : after[0]) work.push_back(make_int4(1, j, 0, 0));
+        for (size_t bi = 0; bi + 1 < after.size(); ++bi) {
+            work.push_back(make_int4(0, (int)(bi * pc), 0, 0));
+            for (int j : after[bi + 1]) work.push_back(make_int4(1, j, 0, 0));
+        }
     }
     int rc = upload_list(b, host, &b->tiles, &b->ntiles);
     if (rc == CLB_OK) rc = upload_list(b, inner, &b->itiles, &b->n_itiles);
     if (rc == CLB_OK) rc = upload_list(b, edges, &b->echunks, &b->n_echunks);
+    if (rc == CLB_OK) rc = upload_list(b, work, &b->work, &b->n_work);
     batch_drop_graphs(b);
     return rc;
 }
 
-// Captured graphs run the edge kernel as a branch parallel to the interior
-// kernel (build-time option; 0 captures the two launches in sequence).
+// FP16 forms: interior tiles and edge chunks in one launch, each edge chunk
+// after the interior block covering its rows (build-time option; 0 launches
+// two kernels, which captured graphs run as parallel branches when
+// CLB_BATCH_FORK is 1).
+#ifndef CLB_BATCH_MIX
+#define CLB_BATCH_MIX 1
+#endif
 #ifndef CLB_BATCH_FORK
 #define CLB_BATCH_FORK 1
 #endif
@@ -143,6 +182,16 @@ static void batch_launch_as(clb_batch* b, cudaStream_t s, cudaStream_t side) {
     const C* tab = (const C*)b->table;
     const dim3 block(kShapes[b->shape][0], kShapes[b->shape][1]);
     if constexpr (NPT == 2) {
+        if (CLB_BATCH_MIX && b->n_work > 0) {
+            const unsigned g = (unsigned)b->n_work;
+            const int4 *w = b->work, *t = b->itiles, *e = b->echunks;
+            const int n = b->n_itiles, pc = b->per_cta, par = b->par;
+            if (b->shift && b->forch) k_step_batch_mix<P, true, true><<<g, block, 0, s>>>(tab, w, t, n, pc, e, par);
+            else if (b->shift) k_step_batch_mix<P, true, false><<<g, block, 0, s>>>(tab, w, t, n, pc, e, par);
+            else if (b->forch) k_step_batch_mix<P, false, true><<<g, block, 0, s>>>(tab, w, t, n, pc, e, par);
+            else k_step_batch_mix<P, false, false><<<g, block, 0, s>>>(tab, w, t, n, pc, e, par);
+            return;
+        }
         const bool fork = side && b->n_itiles > 0 && b->n_echunks > 0;
         cudaStream_t es = s;
         if (fork && cudaEventRecord(b->ev_fork, s) == cudaSuccess && cudaStreamWaitEvent(side, b->ev_fork, 0) == cudaSuccess)
@@ -550,6 +599,7 @@ extern "C" void clb_batch_destroy(clb_batch* b) {
     cudaFree(b->tiles);
     cudaFree(b->itiles);
     cudaFree(b->echunks);
+    cudaFree(b->work);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     if (b->cap_side) cudaStreamDestroy(b->cap_side);
     if (b->ev_fork) cudaEventDestroy(b->ev_fork);

@@ -1409,7 +1409,7 @@ __host__ __device__ inline long long edge_count(const Geo& G) {
     return (G.wall_y ? 2LL * G.nx : 0LL) + (long long)rows * edge_per_row(G.nx);
 }
 
-__device__ __forceinline__ void edge_node(const Geo& G, long long i, int& x, int& y) {
+__host__ __device__ __forceinline__ void edge_node(const Geo& G, long long i, int& x, int& y) {
     if (G.wall_y) {
         if (i < G.nx) { x = (int)i; y = 0; return; }
         if (i < 2LL * G.nx) { x = (int)(i - G.nx); y = G.ny - 1; return; }
@@ -1544,23 +1544,28 @@ __global__ void __launch_bounds__(128, CLB_BATCH_MINB) k_step_batch(const CaseT<
 #ifndef CLB_BATCH_INT_MINB
 #define CLB_BATCH_INT_MINB 5
 #endif
-template <class P, bool SHIFT, bool FORCH>
-__global__ void __launch_bounds__(128, CLB_BATCH_INT_MINB)
-    k_step_batch_int(const CaseT<typename P::R, typename P::S>* __restrict__ cases, const int4* __restrict__ tiles,
-                     int ntiles, int per_cta, int par) {
-    using C = CaseT<typename P::R, typename P::S>;
-    __shared__ __align__(16) unsigned char raw[sizeof(C)];
-    C& sc = *reinterpret_cast<C*>(raw);
+// Loads case c's descriptor into the block's shared copy.
+template <class C>
+__device__ __forceinline__ void load_case(const C* __restrict__ cases, int c, unsigned char* raw) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
-    const int t0 = blockIdx.x * per_cta, t1 = min(t0 + per_cta, ntiles);
+    const unsigned* src = reinterpret_cast<const unsigned*>(cases + c);
+    unsigned* dst = reinterpret_cast<unsigned*>(raw);
+    for (int w = tid; w < (int)(sizeof(C) / 4); w += nthr) dst[w] = __ldg(src + w);
+}
+
+// Interior-pair tiles [t0, t1) of `tiles` (see k_step_batch_int).
+template <class P, bool SHIFT, bool FORCH>
+__device__ __forceinline__ void batch_int_tiles(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
+                                                const int4* __restrict__ tiles, int t0, int t1, int par,
+                                                unsigned char* raw) {
+    using C = CaseT<typename P::R, typename P::S>;
+    C& sc = *reinterpret_cast<C*>(raw);
     int cur = -1;
     for (int t = t0; t < t1; ++t) {
         const int4 tl = __ldg(tiles + t);
         if (tl.x != cur) {
             __syncthreads();
-            const unsigned* src = reinterpret_cast<const unsigned*>(cases + tl.x);
-            unsigned* dst = reinterpret_cast<unsigned*>(raw);
-            for (int w = tid; w < (int)(sizeof(C) / 4); w += nthr) dst[w] = __ldg(src + w);
+            load_case(cases, tl.x, raw);
             __syncthreads();
             cur = tl.x;
         }
@@ -1573,26 +1578,62 @@ __global__ void __launch_bounds__(128, CLB_BATCH_INT_MINB)
     }
 }
 
+// One chunk (case, first edge index, count <= threads of the block) of edge
+// nodes, one per thread (see k_step_batch_edge).
+template <class P, bool SHIFT, bool FORCH>
+__device__ __forceinline__ void batch_edge_chunk(const CaseT<typename P::R, typename P::S>* __restrict__ cases,
+                                                 int4 ch, int par, unsigned char* raw) {
+    using C = CaseT<typename P::R, typename P::S>;
+    C& sc = *reinterpret_cast<C*>(raw);
+    load_case(cases, ch.x, raw);
+    __syncthreads();
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid >= ch.z) return;
+    int x, y;
+    edge_node(sc.K.g, (long long)ch.y + tid, x, y);
+    const int b = par ^ sc.flip;
+    step_node<P, SHIFT, FORCH>(sc.b[b], sc.b[1 - b], sc.A, sc.K, x, y);
+}
+
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, CLB_BATCH_INT_MINB)
+    k_step_batch_int(const CaseT<typename P::R, typename P::S>* __restrict__ cases, const int4* __restrict__ tiles,
+                     int ntiles, int per_cta, int par) {
+    __shared__ __align__(16) unsigned char raw[sizeof(CaseT<typename P::R, typename P::S>)];
+    const int t0 = blockIdx.x * per_cta;
+    batch_int_tiles<P, SHIFT, FORCH>(cases, tiles, t0, min(t0 + per_cta, ntiles), par, raw);
+}
+
 // Edge nodes of a batch (the nodes k_step2 leaves to its per-node path):
 // `chunks` lists (case, first edge index, count) of at most blockDim nodes.
 template <class P, bool SHIFT, bool FORCH>
 __global__ void __launch_bounds__(128, 4)
     k_step_batch_edge(const CaseT<typename P::R, typename P::S>* __restrict__ cases, const int4* __restrict__ chunks,
                       int par) {
-    using C = CaseT<typename P::R, typename P::S>;
-    __shared__ __align__(16) unsigned char raw[sizeof(C)];
-    C& sc = *reinterpret_cast<C*>(raw);
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nthr = blockDim.x * blockDim.y;
-    const int4 ch = __ldg(chunks + blockIdx.x);
-    const unsigned* src = reinterpret_cast<const unsigned*>(cases + ch.x);
-    unsigned* dst = reinterpret_cast<unsigned*>(raw);
-    for (int w = tid; w < (int)(sizeof(C) / 4); w += nthr) dst[w] = __ldg(src + w);
-    __syncthreads();
-    if (tid >= ch.z) return;
-    int x, y;
-    edge_node(sc.K.g, (long long)ch.y + tid, x, y);
-    const int b = par ^ sc.flip;
-    step_node<P, SHIFT, FORCH>(sc.b[b], sc.b[1 - b], sc.A, sc.K, x, y);
+    __shared__ __align__(16) unsigned char raw[sizeof(CaseT<typename P::R, typename P::S>)];
+    batch_edge_chunk<P, SHIFT, FORCH>(cases, __ldg(chunks + blockIdx.x), par, raw);
+}
+
+// Both in one launch: block i takes work[i] = (0, first tile) -- per_cta
+// interior-pair tiles -- or (1, edge chunk).  The host orders the list so
+// that each edge chunk follows the interior block that covers its last row:
+// its column accesses (2 bytes of every 32-byte sector) then find the
+// sectors they share with the neighbouring interior nodes in L2.  In a
+// launch of their own the edge nodes fetched ~13x their bytes from DRAM.
+// The kernel's registers are those of its larger path (the per-node edge
+// step): 4 blocks per SM, where the interior kernel alone runs 5; capped at
+// 5 it spills, and measured slower (36.4 against 37.9 GLUPS on 512 cases).
+#ifndef CLB_BATCH_MIX_MINB
+#define CLB_BATCH_MIX_MINB 4
+#endif
+template <class P, bool SHIFT, bool FORCH>
+__global__ void __launch_bounds__(128, CLB_BATCH_MIX_MINB)
+    k_step_batch_mix(const CaseT<typename P::R, typename P::S>* __restrict__ cases, const int4* __restrict__ work,
+                     const int4* __restrict__ tiles, int ntiles, int per_cta, const int4* __restrict__ chunks, int par) {
+    __shared__ __align__(16) unsigned char raw[sizeof(CaseT<typename P::R, typename P::S>)];
+    const int4 w = __ldg(work + blockIdx.x);
+    if (w.x == 0) batch_int_tiles<P, SHIFT, FORCH>(cases, tiles, w.y, min(w.y + per_cta, ntiles), par, raw);
+    else batch_edge_chunk<P, SHIFT, FORCH>(cases, __ldg(chunks + w.y), par, raw);
 }
 
 // Grid barrier and work counters of the persistent batch launch, in device

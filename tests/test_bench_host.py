@@ -104,7 +104,7 @@ def test_summary_is_compact_and_complete():
     sys.path.insert(0, ROOT)
     import bench
     roof = {"frac": 0.7, "bound": "alu", "fp64_pipe_frac": 0.9}
-    line = {"value": 3000.0, "roofline": roof, "e2e": {"value": 2000.0},
+    line = {"value": 3000.0, "roofline": roof, "e2e": {"value": 2000.0}, "config": {"nx": 4096},
             "forms": {"f16n": {"value": 46000.0, "roofline": {"frac": 0.52}},
                       "f16s": {"value": 77000.0, "roofline": {"frac": 0.68}}},
             "accuracy": {"steps": 1000, **{k: {"rel_err_u": 1e-3, "err_u_over_uc": 2e-5, "max_abs_err_T": 1e-4,
@@ -112,7 +112,7 @@ def test_summary_is_compact_and_complete():
             "accuracy_2048": {"steps": 30000, **{k: {"rel_err_u": 1e-3, "err_u_over_uc": 2e-5,
                                                      "max_abs_err_T": 1e-4, "rel_err_nu": 1e-5}
                                                  for k in ("f16n", "f16s")}},
-            "batch": {"value": 30000.0, "mode": "persistent", "roofline": {"frac": 0.34},
+            "batch": {"value": 30000.0, "cases": 512, "mode": "persistent", "roofline": {"frac": 0.34},
                       "mlups_by_mode": {"graph": 29000.0, "persistent": 30000.0},
                       "validation": {"max_rel_nu_error": 1e-5}},
             "mrt_cost": {"ratio_clb_over_mrt": 1.1}, "cavity64": {"nu_hot": 1.49},
@@ -125,3 +125,8 @@ def test_summary_is_compact_and_complete():
               "cavity64_nu", "steady_128", "oracle_mlups", "warm_start", "surrogate_tflops"):
         assert k in s, k
     assert len(json.dumps(s)) < 1400
+    # keys name the measured sizes
+    line["config"]["nx"] = 2048
+    line["batch"]["cases"] = 128
+    s = bench._summary(line)
+    assert "f64_2048" in s and "batch_128" in s and "f64_4096" not in s
