@@ -262,8 +262,10 @@ FORMS = {  # storage form -> (precision code, algorithmic bytes per coupled cell
 # the node count.  None: not captured for the kernel as it stands.
 FORMS_DRAM_PER_NODE = {"f16n": 75.8, "f16s": 59.7}
 # DRAM bytes (read + write) per node of one launch of the current batch
-# kernel on the 512-case workload (ncu); None: not captured for this kernel.
-BATCH_DRAM_PER_NODE = None
+# kernel (k_step_batch_mix, graph mode), ncu on the first 128 of the 512
+# cases (10.08 M nodes), scaled by the node count; None: not captured for
+# the kernel as it stands.
+BATCH_DRAM_PER_NODE = 80.3
 
 
 def reduced_precision_forms(clb, torch, args, hbm_peak, src):
@@ -356,6 +358,8 @@ def batched_form(clb, torch, args, hbm_peak, src):
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
                         "bytes_per_ccu": bpn,
                         "traffic": BATCH_DRAM_PER_NODE * nodes if BATCH_DRAM_PER_NODE else None,
+                        "traffic_source": "ncu dram bytes per node of k_step_batch_mix on 128 of the cases x nodes "
+                                          "per step",
                         "kernel": "k_step_batch_mix (graph) / k_step_batch_persist <StoreH16N>",
                         "peak_source": f"{src} hbm_gbs"}}
     if args.no_batch_check:
