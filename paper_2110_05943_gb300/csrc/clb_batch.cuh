@@ -4,10 +4,11 @@
 // Each case is an ordinary clb_handle (its own buffers, parameters and
 // reductions); the batch builds a device table of the cases and a tile list
 // over the active ones and advances all of them, in one of two modes:
-//   CLB_BATCH_GRAPH      : one k_step_batch launch per step (FP16 forms:
-//                          k_step_batch_int over the interior-pair tiles
-//                          and k_step_batch_edge over the edge nodes),
-//                          replayed from CUDA graphs of kGraphSteps steps;
+//   CLB_BATCH_GRAPH      : one launch per step -- k_step_batch for FP64,
+//                          k_step_batch_mix for the FP16 forms (blocks of
+//                          interior-pair tiles and blocks of edge nodes in
+//                          one grid) -- replayed from CUDA graphs of
+//                          kGraphSteps steps;
 //   CLB_BATCH_PERSISTENT : one cooperative k_step_batch_persist launch per
 //                          kGraphSteps steps (itself captured in a graph),
 //                          its steps separated by a bounded grid barrier.
