@@ -260,12 +260,12 @@ FORMS = {  # storage form -> (precision code, algorithmic bytes per coupled cell
 # DRAM bytes (read + write) per node of one launch of the current FP16 step
 # kernels, ncu on the 4096^2 case of the same workload; traffic grows with
 # the node count.  None: not captured for the kernel as it stands.
-FORMS_DRAM_PER_NODE = {"f16n": 75.8, "f16s": 59.7}
+FORMS_DRAM_PER_NODE = {"f16n": 76.3, "f16s": 60.3}
 # DRAM bytes (read + write) per node of one launch of the current batch
 # kernel (k_step_batch_mix, graph mode), ncu on the first 128 of the 512
 # cases (10.08 M nodes), scaled by the node count; None: not captured for
 # the kernel as it stands.
-BATCH_DRAM_PER_NODE = 80.3
+BATCH_DRAM_PER_NODE = 80.6
 
 
 def reduced_precision_forms(clb, torch, args, hbm_peak, src):

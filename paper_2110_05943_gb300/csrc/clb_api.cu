@@ -201,11 +201,16 @@ static int map_params(const clb_params* p, clb_lattice* lat, std::string& why) {
     return CLB_OK;
 }
 
-// Block shapes: 64 x 2 threads (FP64, one node each) and 16 x 8 threads
-// (FP16, a node pair each: 32 x 8 nodes; taller blocks reuse the pulled rows
-// y - 1, y, y + 1 in L1, measured 3 % faster than 64 x 2 at 8192^2 F16N).  On
+// Block shapes: 64 x 2 threads for both, one node per thread (FP64) or a
+// node pair (FP16: 128 x 2 nodes, each warp a 128-byte line of every FP16
+// plane).  Measured at 8192^2 with 7 rest-shifted blocks per SM: F16S
+// 78.0 GLUPS with 64-wide blocks, 77.4 with 32 x 4, 76.0 with 16 x 8, 54.6
+// with 8 x 16, 78.1 with 128 x 1; F16N 46.7, 46.7, 46.6, 42.5, 46.6.  On
 // small grids the blocks shrink (to 64 threads at least) until there are two
 // per SM, so a 128^2 cavity is not left on a third of the GPU.
+#ifndef CLB_F16_BX
+#define CLB_F16_BX 64
+#endif
 static void shape_blocks(int units, int ny, int bx, int threads, dim3& block, dim3& grid) {
     const long long want = 2LL * 152;
     while (bx > 32 && bx / 2 >= units) bx /= 2;
@@ -223,7 +228,7 @@ static void shape_blocks(int units, int ny, int bx, int threads, dim3& block, di
 static void pick_launch(clb_handle* h) {
     const int nx = h->prm.nx, ny = h->prm.ny;
     shape_blocks(nx, ny, CLB_F64_BX, CLB_F64_THREADS, h->block, h->grid);
-    shape_blocks((nx + 1) / 2, ny, 16, 128, h->block2, h->grid2);
+    shape_blocks((nx + 1) / 2, ny, CLB_F16_BX, 128, h->block2, h->grid2);
 }
 
 // cuTensorMapEncodeTiled from the driver, looked up once through the runtime

@@ -626,9 +626,42 @@ __device__ __forceinline__ constexpr bool column_dir(int i) { return i == 0 || i
 // before, which the read-only path does not allow; it uses ordinary
 // (coherent) loads, L2-only ones (LdCG) or L1-cached ones (LdCA), made
 // consistent by the acquire fence after its grid barrier.
+// The FP16 forms' read-only loads (halves, half pairs, node records) carry
+// an L2 prefetch-size hint (.L2::256B): a warp's 128-byte line brings its
+// neighbour into L2 with it.  Measured at 8192^2: F16S +0.7 %, F16N +0.4 %,
+// the 512-case batch +0.75 % (0 turns it off; 128 measured no gain).
+#ifndef CLB_LD_L2_PREFETCH
+#define CLB_LD_L2_PREFETCH 256
+#endif
 struct LdNC {
     template <class T>
     static __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+#if CLB_LD_L2_PREFETCH
+#define CLB_STR2_(x) #x
+#define CLB_STR_(x) CLB_STR2_(x)
+#define CLB_L2PF_ ".L2::" CLB_STR_(CLB_LD_L2_PREFETCH) "B"
+    static __device__ __forceinline__ __half ld(const __half* p) {
+        unsigned short v;
+        asm("ld.global.nc" CLB_L2PF_ ".b16 %0, [%1];" : "=h"(v) : "l"(p));
+        return __ushort_as_half(v);
+    }
+    static __device__ __forceinline__ __half2 ld(const __half2* p) {
+        unsigned v;
+        asm("ld.global.nc" CLB_L2PF_ ".b32 %0, [%1];" : "=r"(v) : "l"(p));
+        return *reinterpret_cast<const __half2*>(&v);
+    }
+    static __device__ __forceinline__ uint2 ld(const uint2* p) {
+        uint2 v;
+        asm("ld.global.nc" CLB_L2PF_ ".v2.u32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+        return v;
+    }
+    static __device__ __forceinline__ uint4 ld(const uint4* p) {
+        uint4 v;
+        asm("ld.global.nc" CLB_L2PF_ ".v4.u32 {%0, %1, %2, %3}, [%4];"
+            : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+        return v;
+    }
+#endif
     static __device__ __forceinline__ double ld_again(const double* p) {
         double v;
         asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
@@ -1436,17 +1469,23 @@ __host__ __device__ __forceinline__ void edge_node(const Geo& G, long long i, in
 // that are not interior; the blocks after them take the edge nodes, one per
 // thread, with 128-thread blocks.
 // Resident 128-thread blocks per SM the registers of k_step2 are capped
-// for, per form (measured at 8192^2): the rest-shifted form fits 6 (<= 80
-// registers, 24 warps: 77.1 GLUPS against 74.7 with 5); the
-// equilibrium-shifted form spills below 96 registers (6 blocks: 38.1
-// GLUPS, 5 blocks: 45.9).
+// for, per form (measured at 8192^2 with 64 x 2-thread blocks): the
+// rest-shifted form runs 7 (72 registers, 48 bytes of spills, 28 warps:
+// 78.0 GLUPS against 75.2 with 6 and 73.3 with 8); the equilibrium-shifted
+// form spills below 96 registers (6 blocks: 38.1 GLUPS, 5: 46.7, 4: 46.2).
+#ifndef CLB_F16N_MINB
+#define CLB_F16N_MINB 5
+#endif
 template <class P>
 struct Step2MinBlocks {
-    static constexpr int value = 5;
+    static constexpr int value = CLB_F16N_MINB;
 };
+#ifndef CLB_F16S_MINB
+#define CLB_F16S_MINB 7
+#endif
 template <class L>
 struct Step2MinBlocks<StoreH16T<L>> {
-    static constexpr int value = 6;
+    static constexpr int value = CLB_F16S_MINB;
 };
 
 // OUTER: the pair tiles cover only the rows 0 and ny - 1 (thread rows 0 and
@@ -1462,8 +1501,11 @@ __global__ void __launch_bounds__(128, Step2MinBlocks<P>::value)
         const int x0 = 2 * ((b % tiles_x) * blockDim.x + threadIdx.x);
         int y = (b / tiles_x) * blockDim.y + threadIdx.y;
         if constexpr (OUTER) {
+            // thread row 0 takes row 0 and thread row 1 row ny - 1; a block
+            // of one thread row (small grids) takes both in turn
             if (threadIdx.y > 1) return;
-            y = threadIdx.y == 0 ? 0 : K.g.ny - 1;
+            if (blockDim.y == 1 && interior_pair(K.g, x0, 0)) step_pair_interior<P, SHIFT, FORCH>(in, out, A, K, x0, 0);
+            y = (threadIdx.y == 0 && blockDim.y > 1) ? 0 : K.g.ny - 1;
         }
         if (y >= K.g.ny || !interior_pair(K.g, x0, y)) return;
         step_pair_interior<P, SHIFT, FORCH>(in, out, A, K, x0, y);
