@@ -55,6 +55,33 @@ def test_f16n_random_porosity_ragged_vs_oracle():
     assert e["rho-1"] < 2e-2 and e["ux"] < 4e-3 and e["uy"] < 4e-3 and e["T"] < 7e-4, e
 
 
+@pytest.mark.parametrize("prec,u_uc,dT,nu", [
+    (F16N, 1e-3, 5e-4, 1e-3),   # bench at 2048^2 / 30,000 steps: 3.5e-5, 3.3e-5, 2.3e-5
+    (F16S, 2e-3, 5e-3, 3e-2),   # bench at 2048^2 / 30,000 steps: 8.7e-5, 6.2e-4, 2.6e-3
+])
+def test_f16_forms_on_full_size_blocks_vs_fp64(prec, u_uc, dT, nu):
+    """512^2 seeded cavity (Ra 1e6, Da 1e-3, Pr 0.71, sigma 0.8), 4,000
+    steps, against the FP64 GPU path (parity-tested against the oracle): the
+    grid is large enough for the pair step's full 64 x 2-thread blocks (the
+    smaller grids above run one-row blocks).  Max |u - u64| over the velocity
+    scale u_c = Ma c_s of Eq. 46, max |T - T64| (dT = 1), relative Nu."""
+    from paper_2110_05943_gb300.inputs import porosity_field
+    n = 512
+    phi = porosity_field(n, n, seed=512, ell=16.0)
+    kw = dict(Ra=1e6, Da=1e-3, Pr=0.71, sigma=0.8, with_oracle=False)
+    _, s64 = build(n, n, phi, **kw)
+    _, s16 = build(n, n, phi, precision=prec, **kw)
+    s64.step(4000)
+    s16.step(4000)
+    a, b = s16.macros(), s64.macros()
+    uc = 0.1 / np.sqrt(3.0)
+    eu = max(float(np.max(np.abs(a[k] - b[k]))) for k in (1, 2)) / uc
+    eT = float(np.max(np.abs(a[3] - b[3])))
+    en = abs(s16.nusselt(0) / s64.nusselt(0) - 1)
+    assert np.all(np.isfinite(a[3])) and float(np.max(np.abs(b[1]))) > 1e-6, "no flow to compare"
+    assert eu < u_uc and eT < dT and en < nu, (prec, eu, eT, en)
+
+
 def test_f16n_steady_nusselt_within_1e4_of_fp64():
     """Table 1 row Da 1e-2, Ra 1e4, phi 0.6 on 128^2: steady mean Nusselt
     number of the FP16N form within 1e-4 of the FP64 path."""

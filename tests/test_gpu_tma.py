@@ -45,7 +45,8 @@ def _pair(kind, nx, ny, seed):
     (CAVITY, 128, 66),      # whole tiles (64 x 4 nodes over rows 1 .. 64)
     (CAVITY, 6, 5),         # smaller than one tile: a single interior pair per row
     (CHANNEL_X, 200, 21),   # periodic x: the seam pairs stay with the per-thread kernel
-    (PERIODIC, 96, 40),     # periodic y: rows 0 and ny - 1 too
+    (PERIODIC, 96, 40),     # periodic y: rows 0 and ny - 1 too (one-row blocks: one thread takes both)
+    (PERIODIC, 512, 256),   # full 64 x 2-thread blocks: thread rows 0 and 1 take rows 0 and ny - 1
     (WALLS_X, 70, 33),
 ])
 def test_tma_interior_matches_the_per_thread_path(kind, nx, ny):
